@@ -1,0 +1,713 @@
+/*
+ * kt_oracle.c -- plain, slow, FP64 CPU oracle for per-cell implicit integration of
+ * stiff thermochemical ODEs (Wang 2025, "The Kratos Framework ...", Sec. 2.2-2.3).
+ *
+ * TEST INFRASTRUCTURE.  Only the test-suite, the package smoke check and the
+ * benchmark's CPU-baseline / reference legs may load this library.  The CUDA
+ * library never calls, links or includes it, and it shares no code, header or
+ * table with the CUDA path: it has its own network parser, its own rate law,
+ * Jacobian, Crout LU, Newton iteration, step control and projection.
+ *
+ * Everything is written the obvious way: row-major dense matrices, one cell at a
+ * time, the algorithm's steps in the paper's order.  Threads (pthreads, dynamic
+ * cell counter) only split independent cells.
+ *
+ * What is computed (each function cites the passage it follows):
+ *   ko_rates       modified Arrhenius k(T) and dk/dT          Sec. 2.2.1 item 1
+ *   ko_rhs         dn/dt = sum A n n + sum B n,  dT/dt        Eq. method-ode-thermochem
+ *   ko_jacobian    mass-action + thermal-coupling partials    Eq. method-jacobian, Sec. 2.2.1
+ *   ko_lu          Crout LU, implicit-scaled row pivoting     Algorithm lu-decomp, Sec. 2.3.2
+ *   ko_lu_solve    forward / back substitution                Sec. 2.3.2
+ *   ko_be_solve    one backward-Euler step by Newton          "semi-implicit" solver, Sec. 2.2
+ *   ko_integrate   pre-process, adaptive sub-steps (step       Sec. 2.2.2, 2.2.3, 4.2
+ *                  doubling), clip + conservation projection,
+ *                  retry / revert
+ *
+ * Readings of the paper taken here (the paper is silent or garbled on these):
+ *  - the implicit scheme is backward Euler solved by full Newton; the sub-step
+ *    error is estimated by step doubling (one step h vs two steps h/2), the
+ *    two-half-step result is kept, h_new = h*min(facmax, max(0.2, 0.9/sqrt(err)));
+ *  - Newton converges when |delta_i| <= newton_atol_i + newton_rtol*|y_i| for all i;
+ *    a Newton failure halves h;
+ *  - Arrhenius: k = A (T/T_ref)^b exp(-theta/T); an exponent below -700 gives k = 0;
+ *  - T is the energy variable with a heat capacity per volume C_V = sum_s cv_s n_s
+ *    frozen at the cell's initial abundances, so dT/dt = -sum_s h_s dn_s/dt / C_V;
+ *  - LU pivot ties go to the smallest row index; a zero pivot fails the Newton solve;
+ *  - post-processing clips negatives to zero, then restores the element totals by
+ *    the abundance-weighted least-squares correction dy = -diag(y) N^T lambda,
+ *    (N diag(y) N^T) lambda = N y - b0, which keeps every relative change tiny;
+ *  - retry: from the pre-processed input with h0 * retry_h_factor and
+ *    facmax = retry_facmax; a second failure reverts to the pre-processed input.
+ */
+#include <ctype.h>
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define KO_MAXN 80      /* unknowns per cell (species + T) */
+#define KO_MAXE 8       /* elements */
+#define KO_MAXSIDE 3    /* reactants / products per reaction */
+
+#define KO_OK 0
+#define KO_EINVAL (-1)
+#define KO_ENOMEM (-2)
+#define KO_EPARSE (-4)
+#define KO_ENETWORK (-5)
+
+/* per-cell status */
+#define KO_ST_OK 0
+#define KO_ST_RETRIED 1
+#define KO_ST_REVERTED 2
+#define KO_ST_NONFINITE 3
+
+typedef struct {
+    int ns, ne, nr, energy;
+    double t_ref, t_min, t_max;
+    double *mass, *h, *cv;      /* [ns] */
+    int *counts;                /* [ns*ne] */
+    int *nin, *nout;            /* [nr] */
+    int *in, *out;              /* [nr*KO_MAXSIDE] */
+    double *A, *b, *theta;      /* [nr] */
+} ko_net;
+
+typedef struct {
+    double rtol, atol, h_init, h_min;
+    double newton_rtol, newton_atol_frac;
+    double facmax, retry_h_factor, retry_facmax;
+    int max_substeps, max_newton;
+    int adaptive;   /* 1: step-doubling control; 0: fixed steps of h_init (pins only) */
+    int retry;      /* 1: retry once on failure */
+    int atol_mode;  /* 0: atol absolute; 1: atol times the cell's initial element-0 total */
+    int pad;
+} ko_options;
+
+/* ------------------------------------------------------------------ parsing */
+
+static int next_token(FILE *f, char *buf, int cap)
+{
+    int c, n = 0;
+    for (;;) {
+        c = fgetc(f);
+        if (c == EOF) return 0;
+        if (c == '#') {
+            while (c != '\n' && c != EOF) c = fgetc(f);
+            continue;
+        }
+        if (!isspace(c)) break;
+    }
+    while (c != EOF && !isspace(c) && c != '#') {
+        if (n < cap - 1) buf[n++] = (char)c;
+        c = fgetc(f);
+    }
+    if (c == '#') ungetc(c, f);
+    buf[n] = 0;
+    return 1;
+}
+
+static int expect(FILE *f, const char *word)
+{
+    char buf[256];
+    return next_token(f, buf, sizeof buf) && strcmp(buf, word) == 0;
+}
+
+static int read_int(FILE *f, int *v)
+{
+    char buf[256], *end;
+    if (!next_token(f, buf, sizeof buf)) return 0;
+    long x = strtol(buf, &end, 10);
+    if (*end) return 0;
+    *v = (int)x;
+    return 1;
+}
+
+static int read_dbl(FILE *f, double *v)
+{
+    char buf[256], *end;
+    if (!next_token(f, buf, sizeof buf)) return 0;
+    *v = strtod(buf, &end);
+    return *end == 0;
+}
+
+void ko_free(ko_net *n)
+{
+    if (!n) return;
+    free(n->mass); free(n->h); free(n->cv); free(n->counts);
+    free(n->nin); free(n->nout); free(n->in); free(n->out);
+    free(n->A); free(n->b); free(n->theta);
+    free(n);
+}
+
+int ko_load(const char *path, ko_net **out)
+{
+    char buf[256];
+    int version, i, j;
+    FILE *f = fopen(path, "r");
+    if (!f) return KO_EINVAL;
+    ko_net *n = calloc(1, sizeof *n);
+    if (!n) { fclose(f); return KO_ENOMEM; }
+    int ok = expect(f, "kratos_network") && read_int(f, &version) && version == 1 &&
+             expect(f, "name") && next_token(f, buf, sizeof buf) &&
+             expect(f, "n_species") && read_int(f, &n->ns) &&
+             expect(f, "n_elements") && read_int(f, &n->ne) &&
+             expect(f, "n_reactions") && read_int(f, &n->nr) &&
+             expect(f, "energy") && read_int(f, &n->energy) &&
+             expect(f, "t_ref") && read_dbl(f, &n->t_ref) &&
+             expect(f, "t_min") && read_dbl(f, &n->t_min) &&
+             expect(f, "t_max") && read_dbl(f, &n->t_max) &&
+             expect(f, "elements");
+    if (ok && (n->ns < 1 || n->ne < 1 || n->ne > KO_MAXE || n->nr < 0 ||
+               n->ns + (n->energy ? 1 : 0) > KO_MAXN || (n->energy != 0 && n->energy != 1)))
+        ok = 0;
+    if (!ok) { fclose(f); ko_free(n); return KO_EPARSE; }
+    for (i = 0; i < n->ne && ok; i++) ok = next_token(f, buf, sizeof buf);
+    n->mass = calloc(n->ns, sizeof(double));
+    n->h = calloc(n->ns, sizeof(double));
+    n->cv = calloc(n->ns, sizeof(double));
+    n->counts = calloc((size_t)n->ns * n->ne, sizeof(int));
+    n->nin = calloc(n->nr + 1, sizeof(int));
+    n->nout = calloc(n->nr + 1, sizeof(int));
+    n->in = calloc((size_t)(n->nr + 1) * KO_MAXSIDE, sizeof(int));
+    n->out = calloc((size_t)(n->nr + 1) * KO_MAXSIDE, sizeof(int));
+    n->A = calloc(n->nr + 1, sizeof(double));
+    n->b = calloc(n->nr + 1, sizeof(double));
+    n->theta = calloc(n->nr + 1, sizeof(double));
+    if (!n->mass || !n->h || !n->cv || !n->counts || !n->nin || !n->nout || !n->in ||
+        !n->out || !n->A || !n->b || !n->theta) {
+        fclose(f); ko_free(n); return KO_ENOMEM;
+    }
+    for (i = 0; i < n->ns && ok; i++) {
+        ok = expect(f, "species") && next_token(f, buf, sizeof buf) &&
+             read_dbl(f, &n->mass[i]) && read_dbl(f, &n->h[i]) && read_dbl(f, &n->cv[i]);
+        for (j = 0; j < n->ne && ok; j++) ok = read_int(f, &n->counts[i * n->ne + j]);
+    }
+    for (i = 0; i < n->nr && ok; i++) {
+        int pair;
+        ok = expect(f, "reaction") && read_int(f, &n->nin[i]) &&
+             n->nin[i] >= 1 && n->nin[i] <= KO_MAXSIDE;
+        for (j = 0; j < n->nin[i] && ok; j++)
+            ok = read_int(f, &n->in[i * KO_MAXSIDE + j]) &&
+                 n->in[i * KO_MAXSIDE + j] >= 0 && n->in[i * KO_MAXSIDE + j] < n->ns;
+        ok = ok && read_int(f, &n->nout[i]) && n->nout[i] >= 0 && n->nout[i] <= KO_MAXSIDE;
+        for (j = 0; j < n->nout[i] && ok; j++)
+            ok = read_int(f, &n->out[i * KO_MAXSIDE + j]) &&
+                 n->out[i * KO_MAXSIDE + j] >= 0 && n->out[i * KO_MAXSIDE + j] < n->ns;
+        ok = ok && read_dbl(f, &n->A[i]) && read_dbl(f, &n->b[i]) &&
+             read_dbl(f, &n->theta[i]) && read_int(f, &pair);
+    }
+    ok = ok && expect(f, "end");
+    fclose(f);
+    if (!ok) { ko_free(n); return KO_EPARSE; }
+    /* every reaction must conserve every element (Eq. method-const-elem) */
+    for (i = 0; i < n->nr; i++) {
+        int e;
+        for (e = 0; e < n->ne; e++) {
+            int bal = 0;
+            for (j = 0; j < n->nin[i]; j++) bal -= n->counts[n->in[i * KO_MAXSIDE + j] * n->ne + e];
+            for (j = 0; j < n->nout[i]; j++) bal += n->counts[n->out[i * KO_MAXSIDE + j] * n->ne + e];
+            if (bal != 0) { ko_free(n); return KO_ENETWORK; }
+        }
+    }
+    *out = n;
+    return KO_OK;
+}
+
+int ko_info(const ko_net *n, int *ns, int *ne, int *nr, int *energy)
+{
+    *ns = n->ns; *ne = n->ne; *nr = n->nr; *energy = n->energy;
+    return KO_OK;
+}
+
+/* ------------------------------------------------------------------ rate law */
+
+/* Modified Arrhenius coefficient (Sec. 2.2.1, item 1): k = A (T/T_ref)^b exp(-theta/T),
+ * dk/dT = k (b + theta/T) / T.  Exponents below -700 are flushed to k = 0. */
+int ko_rates(const ko_net *n, double T, double *k, double *dkdT)
+{
+    int r;
+    if (!(T > 0.0)) return KO_EINVAL;
+    double lt = log(T / n->t_ref);
+    for (r = 0; r < n->nr; r++) {
+        double arg = n->b[r] * lt - n->theta[r] / T;
+        if (arg < -700.0) {
+            k[r] = 0.0;
+            dkdT[r] = 0.0;
+        } else {
+            k[r] = n->A[r] * exp(arg);
+            dkdT[r] = k[r] * (n->b[r] + n->theta[r] / T) / T;
+        }
+    }
+    return KO_OK;
+}
+
+/* Right-hand side (Eq. method-ode-thermochem): each reaction's rate is
+ * w_r = k_r * prod(reactant densities); every reactant occurrence loses w_r and
+ * every product occurrence gains w_r.  With the energy equation the last unknown is
+ * T and dT/dt = -sum_s h_s dn_s/dt / C_V. */
+static void rhs(const ko_net *n, const double *y, const double *k, double cvtot, double *f)
+{
+    int N = n->ns + n->energy, r, j;
+    for (j = 0; j < N; j++) f[j] = 0.0;
+    for (r = 0; r < n->nr; r++) {
+        double w = k[r];
+        for (j = 0; j < n->nin[r]; j++) w *= y[n->in[r * KO_MAXSIDE + j]];
+        for (j = 0; j < n->nin[r]; j++) f[n->in[r * KO_MAXSIDE + j]] -= w;
+        for (j = 0; j < n->nout[r]; j++) f[n->out[r * KO_MAXSIDE + j]] += w;
+    }
+    if (n->energy) {
+        double q = 0.0;
+        for (j = 0; j < n->ns; j++) q += n->h[j] * f[j];
+        f[n->ns] = -q / cvtot;
+    }
+}
+
+/* Analytic Jacobian (Eq. method-jacobian and the mass-action derivative cases;
+ * thermal coupling through dk/dT, with dC_V/dn neglected as the paper does). */
+static void jacobian(const ko_net *n, const double *y, const double *k, const double *dkdT,
+                     double cvtot, double *J)
+{
+    int N = n->ns + n->energy, r, j, l, a;
+    for (j = 0; j < N * N; j++) J[j] = 0.0;
+    for (r = 0; r < n->nr; r++) {
+        const int *in = n->in + r * KO_MAXSIDE, *out = n->out + r * KO_MAXSIDE;
+        for (j = 0; j < n->nin[r]; j++) {
+            /* d w_r / d y_m for the reactant occurrence j (m = in[j]) */
+            double d = k[r];
+            for (l = 0; l < n->nin[r]; l++)
+                if (l != j) d *= y[in[l]];
+            int m = in[j];
+            for (a = 0; a < n->nin[r]; a++) J[in[a] * N + m] -= d;
+            for (a = 0; a < n->nout[r]; a++) J[out[a] * N + m] += d;
+        }
+        if (n->energy) {
+            double dT = dkdT[r];
+            for (l = 0; l < n->nin[r]; l++) dT *= y[in[l]];
+            for (a = 0; a < n->nin[r]; a++) J[in[a] * N + n->ns] -= dT;
+            for (a = 0; a < n->nout[r]; a++) J[out[a] * N + n->ns] += dT;
+        }
+    }
+    if (n->energy) {
+        int m;
+        for (m = 0; m < N; m++) {
+            double q = 0.0;
+            for (j = 0; j < n->ns; j++) q += n->h[j] * J[j * N + m];
+            J[n->ns * N + m] = -q / cvtot;
+        }
+    }
+}
+
+int ko_rhs(const ko_net *n, const double *y, double T_iso, double cvtot, double *f)
+{
+    double k[4096], dk[4096];
+    if (n->nr > 4096) return KO_EINVAL;
+    int rc = ko_rates(n, n->energy ? y[n->ns] : T_iso, k, dk);
+    if (rc) return rc;
+    rhs(n, y, k, cvtot, f);
+    return KO_OK;
+}
+
+int ko_jacobian(const ko_net *n, const double *y, double T_iso, double cvtot, double *J)
+{
+    double k[4096], dk[4096];
+    if (n->nr > 4096) return KO_EINVAL;
+    int rc = ko_rates(n, n->energy ? y[n->ns] : T_iso, k, dk);
+    if (rc) return rc;
+    jacobian(n, y, k, dk, cvtot, J);
+    return KO_OK;
+}
+
+/* ------------------------------------------------------------------ linear algebra */
+
+/* Crout LU with implicit-scaled partial pivoting (Algorithm lu-decomp; Numerical
+ * Recipes' ludcmp, which the paper cites).  v_i is the largest |a_ij| of row i.  For
+ * each column j: a_ij -= sum_{k < min(i,j)} a_ik a_kj for every row; the pivot row is
+ * argmax_{i >= j} |a_ij| / v_i (ties: smallest i); rows j and i_max are swapped
+ * (with their scales) and p_j = i_max; then a_ij /= a_jj for i > j.  Returns -1 on a
+ * zero row or a zero pivot. */
+int ko_lu(int N, double *a, int *perm)
+{
+    double v[KO_MAXN];
+    int i, j, k;
+    for (i = 0; i < N; i++) {
+        double big = 0.0;
+        for (j = 0; j < N; j++)
+            if (fabs(a[i * N + j]) > big) big = fabs(a[i * N + j]);
+        if (!(big > 0.0)) return -1;
+        v[i] = big;
+    }
+    for (j = 0; j < N; j++) {
+        for (i = 0; i < N; i++) {
+            int kmax = i < j ? i : j;
+            double s = a[i * N + j];
+            for (k = 0; k < kmax; k++) s -= a[i * N + k] * a[k * N + j];
+            a[i * N + j] = s;
+        }
+        int imax = j;
+        double tmax = fabs(a[j * N + j]) / v[j];
+        for (i = j + 1; i < N; i++) {
+            double t = fabs(a[i * N + j]) / v[i];
+            if (t > tmax) { tmax = t; imax = i; }
+        }
+        if (!(tmax > 0.0)) return -1;
+        if (imax != j) {
+            for (k = 0; k < N; k++) {
+                double tmp = a[imax * N + k];
+                a[imax * N + k] = a[j * N + k];
+                a[j * N + k] = tmp;
+            }
+            double tv = v[imax]; v[imax] = v[j]; v[j] = tv;
+        }
+        perm[j] = imax;
+        for (i = j + 1; i < N; i++) a[i * N + j] /= a[j * N + j];
+    }
+    return 0;
+}
+
+/* Solve with the factors of ko_lu: apply the row swaps in order, then forward
+ * substitution with the unit-diagonal L and back substitution with U. */
+void ko_lu_solve(int N, const double *a, const int *perm, double *x)
+{
+    int i, k;
+    for (i = 0; i < N; i++) {
+        double t = x[i]; x[i] = x[perm[i]]; x[perm[i]] = t;
+    }
+    for (i = 0; i < N; i++) {
+        double s = x[i];
+        for (k = 0; k < i; k++) s -= a[i * N + k] * x[k];
+        x[i] = s;
+    }
+    for (i = N - 1; i >= 0; i--) {
+        double s = x[i];
+        for (k = i + 1; k < N; k++) s -= a[i * N + k] * x[k];
+        x[i] = s / a[i * N + i];
+    }
+}
+
+/* ------------------------------------------------------------------ integrator */
+
+typedef struct {
+    const ko_net *n;
+    const ko_options *o;
+    int N;
+    double T_iso, cvtot;
+    double atol_s;            /* species absolute tolerance for this cell */
+    double k[4096], dk[4096];
+    double f[KO_MAXN], G[KO_MAXN], d[KO_MAXN];
+    double M[KO_MAXN * KO_MAXN], J[KO_MAXN * KO_MAXN];
+    int perm[KO_MAXN];
+    long nnewton;
+} ko_cell;
+
+static double natol(const ko_cell *c, int i)
+{
+    return i < c->n->ns ? c->o->newton_atol_frac * c->atol_s : 0.0;
+}
+
+static double eatol(const ko_cell *c, int i)
+{
+    return i < c->n->ns ? c->atol_s : 0.0;
+}
+
+/* One backward-Euler step y = yn + h f(y), solved by full Newton from the guess in y:
+ * M = I - h J(y), M delta = -(y - yn - h f(y)), y += delta, until every
+ * |delta_i| <= natol_i + newton_rtol |y_i|.  Returns 0 on convergence. */
+static int be_solve(ko_cell *c, const double *yn, double h, double *y)
+{
+    const ko_net *n = c->n;
+    int N = c->N, it, i, j;
+    for (it = 0; it < c->o->max_newton; it++) {
+        c->nnewton++;
+        double T = n->energy ? y[n->ns] : c->T_iso;
+        if (!(T > 0.0)) return -1;
+        ko_rates(n, T, c->k, c->dk);
+        rhs(n, y, c->k, c->cvtot, c->f);
+        for (i = 0; i < N; i++) c->G[i] = y[i] - yn[i] - h * c->f[i];
+        jacobian(n, y, c->k, c->dk, c->cvtot, c->J);
+        for (i = 0; i < N; i++)
+            for (j = 0; j < N; j++)
+                c->M[i * N + j] = (i == j ? 1.0 : 0.0) - h * c->J[i * N + j];
+        if (ko_lu(N, c->M, c->perm)) return -1;
+        for (i = 0; i < N; i++) c->d[i] = -c->G[i];
+        ko_lu_solve(N, c->M, c->perm, c->d);
+        int conv = 1;
+        for (i = 0; i < N; i++) {
+            y[i] += c->d[i];
+            double tol = natol(c, i) + c->o->newton_rtol * fabs(y[i]);
+            if (!(fabs(c->d[i]) <= tol)) conv = 0;
+        }
+        if (conv) return 0;
+    }
+    return -1;
+}
+
+/* Weighted RMS of the step-doubling difference, weights atol_i + rtol max(|y_i|,|y2_i|). */
+static double err_norm(const ko_cell *c, const double *y, const double *y2, const double *yf)
+{
+    double s = 0.0;
+    int i;
+    for (i = 0; i < c->N; i++) {
+        double sc = eatol(c, i) + c->o->rtol * fmax(fabs(y[i]), fabs(y2[i]));
+        double e = (y2[i] - yf[i]) / sc;
+        s += e * e;
+    }
+    return sqrt(s / c->N);
+}
+
+#define ADV_OK 0
+#define ADV_FAIL 1
+
+/* Advance y over [0, dt] with adaptive sub-steps (or fixed steps when adaptive=0). */
+static int advance(ko_cell *c, double *y, double dt, double h0, double facmax, int *nsub)
+{
+    const ko_options *o = c->o;
+    int N = c->N, i;
+    double yf[KO_MAXN], yh[KO_MAXN], y2[KO_MAXN];
+    double t = 0.0, h = h0;
+    int nacc = 0, natt = 0;
+    for (;;) {
+        if (natt >= o->max_substeps) return ADV_FAIL;
+        natt++;
+        int last = 0;
+        if (t + h >= dt * (1.0 - 1e-12)) { h = dt - t; last = 1; }
+        if (!o->adaptive) {
+            for (i = 0; i < N; i++) yf[i] = y[i];
+            if (be_solve(c, y, h, yf)) return ADV_FAIL;
+            for (i = 0; i < N; i++) y[i] = yf[i];
+            nacc++;
+            if (last) break;
+            t += h;
+            continue;
+        }
+        for (i = 0; i < N; i++) yf[i] = y[i];
+        int ok = be_solve(c, y, h, yf) == 0;
+        if (ok) {
+            for (i = 0; i < N; i++) yh[i] = y[i];
+            ok = be_solve(c, y, 0.5 * h, yh) == 0;
+        }
+        if (ok) {
+            for (i = 0; i < N; i++) y2[i] = yh[i];
+            ok = be_solve(c, yh, 0.5 * h, y2) == 0;
+        }
+        if (!ok) {
+            h *= 0.5;
+            if (h < o->h_min) return ADV_FAIL;
+            continue;
+        }
+        double err = err_norm(c, y, y2, yf);
+        if (err <= 1.0) {
+            for (i = 0; i < N; i++) y[i] = y2[i];
+            nacc++;
+            if (last) break;
+            t += h;
+            double fac = err > 0.0 ? 0.9 / sqrt(err) : facmax;
+            if (fac > facmax) fac = facmax;
+            if (fac < 0.2) fac = 0.2;
+            h *= fac;
+        } else {
+            double fac = 0.9 / sqrt(err);   /* NaN err falls through to the 0.2 clamp */
+            if (!(fac >= 0.2)) fac = 0.2;
+            h *= fac;
+            if (h < o->h_min) return ADV_FAIL;
+        }
+    }
+    *nsub = nacc;
+    return ADV_OK;
+}
+
+/* Small dense solve for the projection (Gaussian elimination, partial pivoting). */
+static int small_solve(int m, double *A, double *x)
+{
+    int i, j, k;
+    for (k = 0; k < m; k++) {
+        int p = k;
+        for (i = k + 1; i < m; i++)
+            if (fabs(A[i * m + k]) > fabs(A[p * m + k])) p = i;
+        if (!(fabs(A[p * m + k]) > 0.0)) return -1;
+        if (p != k) {
+            for (j = 0; j < m; j++) { double t = A[k * m + j]; A[k * m + j] = A[p * m + j]; A[p * m + j] = t; }
+            double t = x[k]; x[k] = x[p]; x[p] = t;
+        }
+        for (i = k + 1; i < m; i++) {
+            double l = A[i * m + k] / A[k * m + k];
+            for (j = k; j < m; j++) A[i * m + j] -= l * A[k * m + j];
+            x[i] -= l * x[k];
+        }
+    }
+    for (i = m - 1; i >= 0; i--) {
+        double s = x[i];
+        for (j = i + 1; j < m; j++) s -= A[i * m + j] * x[j];
+        x[i] = s / A[i * m + i];
+    }
+    return 0;
+}
+
+/* Post-processing (Sec. 2.2.3): stage 1 clips negative abundances; the element
+ * totals b0 of the initial state are then restored by y_s -= y_s (N^T lambda)_s with
+ * (N diag(y) N^T) lambda = N y - b0.  An element with no abundance left must have a
+ * zero defect; a relative correction >= 1 (it would empty a species) is a
+ * conservation failure. */
+static int post_process(const ko_cell *c, double *y, const double *b0)
+{
+    const ko_net *n = c->n;
+    int ns = n->ns, ne = n->ne, s, e, f;
+    double M[KO_MAXE * KO_MAXE], r[KO_MAXE];
+    for (s = 0; s < ns; s++)
+        if (y[s] < 0.0) y[s] = 0.0;
+    for (e = 0; e < ne; e++) {
+        double tot = 0.0;
+        for (s = 0; s < ns; s++) tot += n->counts[s * ne + e] * y[s];
+        r[e] = tot - b0[e];
+        for (f = 0; f < ne; f++) {
+            double m = 0.0;
+            for (s = 0; s < ns; s++) m += (double)n->counts[s * ne + e] * n->counts[s * ne + f] * y[s];
+            M[e * ne + f] = m;
+        }
+    }
+    for (e = 0; e < ne; e++) {
+        if (M[e * ne + e] == 0.0) {
+            if (r[e] != 0.0) return -1;
+            for (f = 0; f < ne; f++) M[e * ne + f] = M[f * ne + e] = 0.0;
+            M[e * ne + e] = 1.0;
+        }
+    }
+    if (small_solve(ne, M, r)) return -1;
+    for (s = 0; s < ns; s++) {
+        double corr = 0.0;
+        for (e = 0; e < ne; e++) corr += n->counts[s * ne + e] * r[e];
+        if (!(corr < 1.0)) return -1;
+        y[s] -= y[s] * corr;
+    }
+    for (s = 0; s < c->N; s++)
+        if (!isfinite(y[s])) return -1;
+    return 0;
+}
+
+/* One cell: pre-process, integrate, post-process, retry / revert (Sec. 2.2.2-2.2.3). */
+static void integrate_cell(const ko_net *n, const ko_options *o, double dt,
+                           const double *yin, double Tin, double *yout, double *Tout,
+                           int32_t *status, int32_t *nsub, int32_t *nnew, ko_cell *c)
+{
+    int ns = n->ns, N = ns + n->energy, s, e;
+    double y0[KO_MAXN], y[KO_MAXN], b0[KO_MAXE];
+    int finite = isfinite(Tin);
+    for (s = 0; s < ns; s++) finite = finite && isfinite(yin[s]);
+    c->n = n; c->o = o; c->N = N; c->nnewton = 0;
+    if (!finite) {
+        for (s = 0; s < ns; s++) yout[s] = yin[s];
+        *Tout = Tin; *status = KO_ST_NONFINITE; *nsub = 0; *nnew = 0;
+        return;
+    }
+    /* pre-processing: floors and temperature limits */
+    for (s = 0; s < ns; s++) y0[s] = yin[s] > 0.0 ? yin[s] : 0.0;
+    double T0 = Tin < n->t_min ? n->t_min : (Tin > n->t_max ? n->t_max : Tin);
+    if (n->energy) y0[ns] = T0;
+    c->T_iso = T0;
+    for (e = 0; e < n->ne; e++) {
+        double t = 0.0;
+        for (s = 0; s < ns; s++) t += n->counts[s * n->ne + e] * y0[s];
+        b0[e] = t;
+    }
+    c->cvtot = 0.0;
+    for (s = 0; s < ns; s++) c->cvtot += n->cv[s] * y0[s];
+    c->atol_s = o->atol;
+    if (o->atol_mode == 1 && b0[0] > 0.0) c->atol_s = o->atol * b0[0];
+
+    int st = KO_ST_OK, ns_ok = 0;
+    for (s = 0; s < N; s++) y[s] = y0[s];
+    int rc = advance(c, y, dt, o->h_init, o->facmax, &ns_ok);
+    if (rc == ADV_OK) rc = post_process(c, y, b0) ? ADV_FAIL : ADV_OK;
+    if (rc != ADV_OK && o->retry) {
+        for (s = 0; s < N; s++) y[s] = y0[s];
+        rc = advance(c, y, dt, o->h_init * o->retry_h_factor, o->retry_facmax, &ns_ok);
+        if (rc == ADV_OK) rc = post_process(c, y, b0) ? ADV_FAIL : ADV_OK;
+        st = KO_ST_RETRIED;
+    }
+    if (rc != ADV_OK) {
+        for (s = 0; s < N; s++) y[s] = y0[s];
+        st = KO_ST_REVERTED;
+        ns_ok = 0;
+    }
+    for (s = 0; s < ns; s++) yout[s] = y[s];
+    *Tout = n->energy ? y[ns] : T0;
+    *status = st;
+    *nsub = ns_ok;
+    *nnew = c->nnewton > 2147483647L ? 2147483647 : (int32_t)c->nnewton;
+}
+
+typedef struct {
+    const ko_net *n;
+    const ko_options *o;
+    double dt;
+    int64_t ncells;
+    const double *y, *T;
+    double *yo, *To;
+    int32_t *st, *nsub, *nnew;
+    int64_t next;
+    pthread_mutex_t lock;
+} ko_job;
+
+static void *worker(void *arg)
+{
+    ko_job *jb = arg;
+    ko_cell *c = malloc(sizeof *c);
+    double yin[KO_MAXN], yout[KO_MAXN];
+    int ns = jb->n->ns, s;
+    if (!c) return NULL;
+    for (;;) {
+        pthread_mutex_lock(&jb->lock);
+        int64_t i = jb->next++;
+        pthread_mutex_unlock(&jb->lock);
+        if (i >= jb->ncells) break;
+        for (s = 0; s < ns; s++) yin[s] = jb->y[(int64_t)s * jb->ncells + i];
+        double To;
+        integrate_cell(jb->n, jb->o, jb->dt, yin, jb->T[i], yout, &To, &jb->st[i],
+                       &jb->nsub[i], &jb->nnew[i], c);
+        for (s = 0; s < ns; s++) jb->yo[(int64_t)s * jb->ncells + i] = yout[s];
+        jb->To[i] = To;
+    }
+    free(c);
+    return NULL;
+}
+
+/* Integrate ncells cells over dt.  y, y_out: [ns][ncells] SoA; T, T_out: [ncells].
+ * rho is accepted for interface symmetry and unused by the ODE.  nthreads <= 0 means 1. */
+int ko_integrate(const ko_net *n, int64_t ncells, const double *y, const double *T,
+                 const double *rho, double dt, const ko_options *o, int nthreads,
+                 double *y_out, double *T_out, int32_t *status, int32_t *nsub, int32_t *nnew)
+{
+    (void)rho;
+    if (!n || !o || ncells < 0 || !(dt > 0.0) || !(o->atol > 0.0) || !(o->rtol > 0.0) ||
+        o->max_newton < 1 || o->max_substeps < 1 || !(o->h_init > 0.0))
+        return KO_EINVAL;
+    if (ncells == 0) return KO_OK;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 512) nthreads = 512;
+    ko_job jb = {n, o, dt, ncells, y, T, y_out, T_out, status, nsub, nnew, 0,
+                 PTHREAD_MUTEX_INITIALIZER};
+    pthread_t th[512];
+    int t, started = 0;
+    for (t = 1; t < nthreads; t++)
+        if (pthread_create(&th[t], NULL, worker, &jb) == 0) started = t;
+        else break;
+    worker(&jb);
+    for (t = 1; t <= started; t++) pthread_join(th[t], NULL);
+    return KO_OK;
+}
+
+/* One backward-Euler step of one cell (pins): y_out = root of y - yn - h f(y). */
+int ko_be_step(const ko_net *n, const ko_options *o, const double *yn, double T_iso,
+               double cvtot, double h, double *y_out, int *n_iter)
+{
+    ko_cell *c = malloc(sizeof *c);
+    int i, rc;
+    if (!c) return KO_ENOMEM;
+    c->n = n; c->o = o; c->N = n->ns + n->energy; c->T_iso = T_iso; c->cvtot = cvtot;
+    c->atol_s = o->atol; c->nnewton = 0;
+    for (i = 0; i < c->N; i++) y_out[i] = yn[i];
+    rc = be_solve(c, yn, h, y_out);
+    *n_iter = (int)c->nnewton;
+    free(c);
+    return rc;
+}

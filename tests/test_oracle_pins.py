@@ -1,0 +1,372 @@
+"""Pins of the FP64 CPU oracle against what the paper and mathematics fix.
+
+Nothing here compares the oracle with itself.  Each pin is a closed form, a library
+routine on a special case, exact rational arithmetic, a printed constant of the
+paper, or an invariant of the ODE class (Sec. 2.2):
+
+* Crout LU (Algorithm lu-decomp): exact rational solutions of integer systems,
+  P A = L U to rounding, the implicit-scaled pivot choice, singular detection.
+* rate law (Sec. 2.2.1): the paper's Stromgren coefficients (Eq. thermo-strom).
+* right-hand side (Eq. method-ode-thermochem): Robertson's textbook equations.
+* Jacobian (Eq. method-jacobian): central finite differences of the right-hand side.
+* backward Euler at fixed h: (I - hK)^-n y0 for a linear decay chain.
+* adaptive control: Bateman closed form, first-order error scaling (~ sqrt(rtol)).
+* Robertson at t = 1e4 against scipy's Radau at rtol 1e-13.
+* invariants: element totals (1e-12), energy (1e-12), non-negativity,
+  detailed balance at long times, the Stromgren ionisation root (Eq. strom-equil).
+* failure path (Sec. 2.2.3): non-finite input, revert, retry.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+from paper_2504_04941_gb300 import inputs as I
+
+EPS = np.finfo(float).eps
+
+
+# ------------------------------------------------------------------ LU
+
+
+def _exact_solve(A, b):
+    """Gauss-Jordan in exact rational arithmetic (brute force, tiny systems)."""
+    n = len(A)
+    M = [[Fraction(int(A[i][j])) for j in range(n)] + [Fraction(int(b[i]))] for i in range(n)]
+    for c in range(n):
+        p = next(r for r in range(c, n) if M[r][c] != 0)
+        M[c], M[p] = M[p], M[c]
+        for r in range(n):
+            if r != c and M[r][c] != 0:
+                f = M[r][c] / M[c][c]
+                M[r] = [M[r][k] - f * M[c][k] for k in range(n + 1)]
+    return [M[i][n] / M[i][i] for i in range(n)]
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 11, 16])
+def test_lu_exact_rational(oracle_mod, n):
+    rng = np.random.default_rng(100 + n)
+    for _ in range(5):
+        A = rng.integers(-9, 10, size=(n, n)).astype(float)
+        if abs(np.linalg.det(A)) < 0.5:
+            A += np.eye(n) * 7
+        b = rng.integers(-20, 21, size=n).astype(float)
+        x_ex = np.array([float(v) for v in _exact_solve(A, b)])
+        rc, fac, perm = oracle_mod.lu(A)
+        assert rc == 0
+        x = oracle_mod.lu_solve(fac, perm, b)
+        assert np.allclose(x, x_ex, rtol=1e-11, atol=1e-11 * np.abs(x_ex).max())
+
+
+def _reconstruct(fac, perm, n):
+    L = np.tril(fac, -1) + np.eye(n)
+    U = np.triu(fac)
+    P = np.eye(n)
+    for j in range(n):
+        P[[j, perm[j]]] = P[[perm[j], j]]
+    return P, L, U
+
+
+@pytest.mark.parametrize("n", [3, 11, 33, 65])
+def test_lu_pa_equals_lu_ill_scaled(oracle_mod, n):
+    """Rows scaled over 16 decades: P A = L U to ~ N eps ||A|| and the solve matches LAPACK."""
+    rng = np.random.default_rng(7 + n)
+    A = rng.standard_normal((n, n)) * 10.0 ** rng.uniform(-8, 8, size=(n, 1))
+    rc, fac, perm = oracle_mod.lu(A)
+    assert rc == 0
+    P, L, U = _reconstruct(fac, perm, n)
+    R = P @ A - L @ U
+    row_scale = np.abs(A).max(axis=1, keepdims=True)
+    # residual row-wise relative to that row's scale
+    assert np.all(np.abs(R) <= 20 * n * EPS * (P @ row_scale))
+    b = rng.standard_normal(n)
+    x = oracle_mod.lu_solve(fac, perm, b)
+    x_ref = np.linalg.solve(A, b)
+    cond = np.linalg.cond(A / row_scale)
+    assert np.allclose(x, x_ref, rtol=100 * n * EPS * cond, atol=0)
+
+
+def test_lu_scaled_pivot_choice(oracle_mod):
+    # unscaled pivoting would take row 0 (|2| > |1|); implicit scaling takes row 1
+    rc, fac, perm = oracle_mod.lu([[2.0, 1e6], [1.0, 1.0]])
+    assert rc == 0 and perm[0] == 1
+    # a tie |a_i0| / v_i = 1 for both rows goes to the smaller index
+    rc, fac, perm = oracle_mod.lu([[1.0, 0.5], [2.0, 1.5]])
+    assert rc == 0 and perm[0] == 0
+
+
+def test_lu_singular(oracle_mod):
+    assert oracle_mod.lu([[1.0, 2.0], [2.0, 4.0]])[0] == -1
+    assert oracle_mod.lu([[0.0, 0.0], [1.0, 1.0]])[0] == -1
+
+
+# ------------------------------------------------------------------ rates / rhs / Jacobian
+
+
+def _golden_stromgren():
+    path = os.path.join(os.path.dirname(__file__), "golden", "stromgren_constants.txt")
+    vals = {}
+    for line in open(path):
+        line = line.split("#")[0].split()
+        if line:
+            vals[line[0]] = float(line[1])
+    return vals
+
+
+def test_rates_stromgren_printed_constants(oracle_mod):
+    g = _golden_stromgren()
+    photo = 3.3e-8
+    net = oracle_mod.OracleNetwork(I.stromgren_network(photo))
+    kb_ev = 8.617333262e-5
+    for T in (300.0, 5000.0, 1.0e4, 2.0e4):
+        k, dk = net.rates(T)
+        alpha = g["alpha_coeff"] * (T / g["t_ref"]) ** g["alpha_exp"]
+        kci = g["kci_coeff"] * (T / g["t_ref"]) ** g["kci_exp"] * math.exp(-g["I_H"] / (kb_ev * T))
+        assert k[0] == photo
+        assert k[2] == pytest.approx(alpha, rel=1e-14)
+        if kci > 1e-300:
+            assert k[1] == pytest.approx(kci, rel=1e-12)
+        # dk/dT against central differences of the printed formulas
+        hT = 1e-5 * T
+        a_p = g["alpha_coeff"] * ((T + hT) / 300) ** -0.75
+        a_m = g["alpha_coeff"] * ((T - hT) / 300) ** -0.75
+        assert dk[2] == pytest.approx((a_p - a_m) / (2 * hT), rel=1e-8)
+    k, _ = net.rates(300.0)
+    assert k[2] == 3.5e-12  # alpha(300 K) is the printed coefficient itself
+
+
+def test_rates_underflow_flush(oracle_mod):
+    net = oracle_mod.OracleNetwork(I.stromgren_network(0.0))
+    k, dk = net.rates(20.0)       # exp(-157821/20) underflows: flushed to exactly 0
+    assert k[1] == 0.0 and dk[1] == 0.0
+
+
+def test_rhs_robertson_textbook(oracle_mod):
+    net = oracle_mod.OracleNetwork(I.robertson_network())
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        y = rng.uniform(0, 1, 3) * np.array([1, 1e-4, 1])
+        f = net.rhs(y)
+        ref = np.array([-0.04 * y[0] + 1e4 * y[1] * y[2],
+                        0.04 * y[0] - 1e4 * y[1] * y[2] - 3e7 * y[1] ** 2,
+                        3e7 * y[1] ** 2])
+        assert np.allclose(f, ref, rtol=1e-14, atol=1e-17)
+
+
+def _fd_jacobian(net, y, T_iso, cvtot):
+    n = len(y)
+    J = np.zeros((n, n))
+    floor = 1e-6 * np.abs(y).max()
+    for m in range(n):
+        h = 1e-6 * max(abs(y[m]), floor)
+        yp, ym = y.copy(), y.copy()
+        yp[m] += h
+        ym[m] -= h
+        J[:, m] = (net.rhs(yp, T_iso, cvtot) - net.rhs(ym, T_iso, cvtot)) / (2 * h)
+    return J
+
+
+@pytest.mark.parametrize("wid", [1, 2, 3, 5])
+def test_jacobian_vs_central_differences(oracle_mod, wid):
+    netw = I.network(wid)
+    net = oracle_mod.OracleNetwork(netw)
+    wl = I.workload(wid, 6) if wid != 5 else I.workload(5, 6)
+    for c in range(3):
+        y = wl.cells.y[:, c].copy()
+        T = float(wl.cells.T[c])
+        cvtot = float(np.dot(netw.cv, y)) if netw.energy else 1.0
+        if netw.energy:
+            y = np.append(y, T)
+        J = net.jacobian(y, T, cvtot)
+        Jfd = _fd_jacobian(net, y, T, cvtot)
+        scale = np.abs(J).max(axis=1, keepdims=True) + 1e-300
+        assert np.all(np.abs(J - Jfd) <= 1e-6 * scale + 1e-6 * np.abs(J)), (wid, c)
+
+
+def test_energy_row_is_heat_release(oracle_mod):
+    """dT/dt = -sum_s h_s dn_s/dt / C_V: C_V f_T + sum h_s f_s = 0 (energy invariant)."""
+    netw = I.network(2)
+    net = oracle_mod.OracleNetwork(netw)
+    wl = I.workload(2, 4)
+    for c in range(4):
+        y = np.append(wl.cells.y[:, c], wl.cells.T[c])
+        cv = float(np.dot(netw.cv, wl.cells.y[:, c]))
+        f = net.rhs(y, 0.0, cv)
+        q = np.dot(netw.h, f[:-1])
+        assert abs(cv * f[-1] + q) <= 1e-12 * np.abs(netw.h * f[:-1]).sum()
+
+
+# ------------------------------------------------------------------ time stepping
+
+
+def test_backward_euler_fixed_step_linear_chain(oracle_mod):
+    """BE at fixed h on A -> B -> C is y_n = (I - hK)^-n y0 exactly (to rounding)."""
+    k1, k2 = 2.0, 50.0
+    net = oracle_mod.OracleNetwork(I.decay_chain_network(k1, k2))
+    K = np.array([[-k1, 0, 0], [k1, -k2, 0], [0, k2, 0]])
+    y0 = np.array([0.7, 0.2, 0.1])
+    h, nsteps = 0.01, 100
+    cells = I.Cells(y0.reshape(3, 1).copy(), np.array([300.0]), np.array([1.0]))
+    opts = oracle_mod.options(rtol=1e-6, atol=1e-14, h_init=h, h_min=1e-30, adaptive=0,
+                              retry=0, newton_rtol=1e-14)
+    r = net.integrate(cells, h * nsteps, opts, nthreads=1)
+    ref = np.linalg.matrix_power(np.linalg.inv(np.eye(3) - h * K), nsteps) @ y0
+    assert r["status"][0] == 0 and r["nsub"][0] == nsteps
+    assert np.allclose(r["y"][:, 0], ref, rtol=1e-13, atol=1e-16)
+
+
+def test_bateman_adaptive_first_order_scaling(oracle_mod):
+    """Step-doubling BE reaches the Bateman solution with error ~ C sqrt(rtol)."""
+    k1, k2, t = 1.0, 10.0, 2.0
+    net = oracle_mod.OracleNetwork(I.decay_chain_network(k1, k2))
+    cells = I.Cells(np.array([[1.0], [0.0], [0.0]]), np.array([300.0]), np.array([1.0]))
+    A = math.exp(-k1 * t)
+    B = k1 / (k2 - k1) * (math.exp(-k1 * t) - math.exp(-k2 * t))
+    ref = np.array([A, B, 1 - A - B])
+    errs = []
+    rtols = [1e-4, 1e-5, 1e-6, 1e-7]
+    for rtol in rtols:
+        r = net.integrate(cells, t, oracle_mod.options(rtol=rtol, atol=1e-14, h_init=1e-6), 1)
+        errs.append(np.abs(r["y"][:, 0] / ref - 1).max())
+        assert errs[-1] <= 2.0 * math.sqrt(rtol)
+    slope = np.polyfit(np.log10(rtols), np.log10(errs), 1)[0]
+    assert 0.45 <= slope <= 0.55, slope
+
+
+def test_robertson_vs_radau(oracle_mod):
+    from scipy.integrate import solve_ivp
+    wl = I.workload(1, 3)
+    net = oracle_mod.OracleNetwork(wl.network)
+
+    def f(t, y):
+        return [-0.04 * y[0] + 1e4 * y[1] * y[2],
+                0.04 * y[0] - 1e4 * y[1] * y[2] - 3e7 * y[1] ** 2, 3e7 * y[1] ** 2]
+
+    def jac(t, y):
+        return [[-0.04, 1e4 * y[2], 1e4 * y[1]],
+                [0.04, -1e4 * y[2] - 6e7 * y[1], -1e4 * y[1]], [0, 6e7 * y[1], 0]]
+
+    errs = {}
+    for rtol in (1e-6, 1e-8):
+        r = net.integrate(wl.cells, 1e4, oracle_mod.options(wl.tol, rtol=rtol), 3)
+        e = 0.0
+        for c in range(3):
+            s = solve_ivp(f, (0, 1e4), wl.cells.y[:, c], method="Radau", rtol=1e-13,
+                          atol=1e-22, jac=jac)
+            ref = s.y[:, -1]
+            e = max(e, np.abs(r["y"][:, c] / ref - 1).max())
+            # conservation y1 + y2 + y3 (one pseudo-element) to rounding
+            assert abs(r["y"][:, c].sum() - wl.cells.y[:, c].sum()) <= 1e-14
+        errs[rtol] = e
+        assert e <= math.sqrt(rtol), (rtol, e)
+    assert errs[1e-8] < errs[1e-6] / 5
+
+
+@pytest.mark.parametrize("wid", [2, 3])
+def test_element_and_energy_conservation(oracle_mod, wid):
+    wl = I.workload(wid, 12)
+    netw = wl.network
+    net = oracle_mod.OracleNetwork(netw)
+    r = net.integrate(wl.cells, wl.tol.dt, oracle_mod.options(wl.tol), 4)
+    assert np.all(r["status"] == 0)
+    y0 = np.maximum(wl.cells.y, 0)
+    b0 = netw.counts.T @ y0
+    b1 = netw.counts.T @ r["y"]
+    # element totals to 1e-12 of the element total, for every element with atoms
+    assert np.all(np.abs(b1 - b0) <= 1e-12 * (netw.counts.T.__abs__() @ y0) + 0.0)
+    assert np.all(r["y"] >= 0.0)
+    if netw.energy:
+        cv = netw.cv @ y0
+        E0 = cv * wl.cells.T + netw.h @ y0
+        E1 = cv * r["T"] + netw.h @ r["y"]
+        mag = cv * wl.cells.T + np.abs(netw.h) @ y0
+        assert np.all(np.abs(E1 - E0) <= 1e-12 * mag)
+
+
+def test_detailed_balance_long_time(oracle_mod):
+    """After a long step every reversible pair balances: k_f prod(r) = k_r prod(p)."""
+    netw = I.network(2)
+    net = oracle_mod.OracleNetwork(netw)
+    wl = I.workload(2, 2)
+    r = net.integrate(wl.cells, 1.0, oracle_mod.options(wl.tol, max_substeps=400000), 2)
+    assert np.all(r["status"] == 0)
+    for c in range(2):
+        y, T = r["y"][:, c], r["T"][c]
+        k, _ = net.rates(T)
+        for q in range(0, netw.nr, 2):
+            wf = k[q] * np.prod([y[i] for i in netw.reac_in[q]])
+            wr = k[q + 1] * np.prod([y[i] for i in netw.reac_in[q + 1]])
+            assert abs(wf - wr) <= 1e-6 * max(wf, wr) + 1e-300
+
+
+@pytest.mark.parametrize("T,photo", [(1.0e4, 1e-9), (8000.0, 1e-12), (2.0e4, 1e-10)])
+def test_stromgren_ionisation_root(oracle_mod, T, photo):
+    """Isothermal H/H+/e- at t >> 1/(alpha n): x_e solves Eq. strom-equil (ionisation line)."""
+    g = _golden_stromgren()
+    n = g["n_amb"]
+    net = oracle_mod.OracleNetwork(I.stromgren_network(photo))
+    cells = I.Cells(np.array([[n * 0.999], [n * 0.001], [n * 0.001]]), np.array([T]),
+                    np.array([n]))
+    r = net.integrate(cells, 1e16, oracle_mod.options(rtol=1e-8, atol=1e-20, h_init=1.0,
+                                                       max_substeps=400000), 1)
+    assert r["status"][0] == 0
+    xe = r["y"][2, 0] / n
+    kb_ev = 8.617333262e-5
+    alpha = g["alpha_coeff"] * (T / g["t_ref"]) ** g["alpha_exp"]
+    kci = g["kci_coeff"] * (T / g["t_ref"]) ** g["kci_exp"] * math.exp(-g["I_H"] / (kb_ev * T))
+    # 0 = alpha n^2 x^2 - kci n^2 x (1-x) - photo n (1-x)   (divide by n)
+    a2 = alpha * n + kci * n
+    a1 = photo - kci * n
+    a0 = -photo
+    x_root = (-a1 + math.sqrt(a1 * a1 - 4 * a2 * a0)) / (2 * a2)
+    assert xe == pytest.approx(x_root, rel=1e-8)
+    assert r["y"][0, 0] + r["y"][1, 0] == pytest.approx(n, rel=1e-13)
+
+
+# ------------------------------------------------------------------ failure path
+
+
+def test_nonfinite_input_status(oracle_mod):
+    wl = I.workload(1, 4)
+    wl.cells.y[0, 1] = np.nan
+    wl.cells.T[2] = np.inf
+    net = oracle_mod.OracleNetwork(wl.network)
+    r = net.integrate(wl.cells, 1.0, oracle_mod.options(wl.tol), 1)
+    assert list(r["status"]) == [0, 3, 3, 0]
+    assert np.isnan(r["y"][0, 1]) and r["nsub"][1] == 0
+
+
+def test_revert_and_retry(oracle_mod):
+    wl = I.workload(1, 2)
+    net = oracle_mod.OracleNetwork(wl.network)
+    # far too few sub-steps: both attempts fail -> revert to the input
+    r = net.integrate(wl.cells, 1e4, oracle_mod.options(wl.tol, max_substeps=50), 1)
+    assert np.all(r["status"] == 2)
+    assert np.array_equal(r["y"], wl.cells.y)
+    # a first attempt that dies on h_min (huge first step, tiny h_min) and a retry
+    # from a much smaller first step that succeeds
+    r = net.integrate(wl.cells, 1e4, oracle_mod.options(wl.tol, h_init=1e3, h_min=1e2,
+                                                        retry_h_factor=1e-9), 1)
+    assert np.all(r["status"] == 1), r["status"]
+
+
+def test_negative_input_clipped_and_T_clamped(oracle_mod):
+    wl = I.workload(2, 2)
+    wl.cells.y[3, 0] = -1e-9
+    wl.cells.T[1] = 1e7
+    net = oracle_mod.OracleNetwork(wl.network)
+    r = net.integrate(wl.cells, 1e-12, oracle_mod.options(wl.tol), 1)
+    assert np.all(r["status"] == 0)
+    assert r["y"][3, 0] >= 0.0
+    assert r["T"][1] <= wl.network.t_max * 1.5
+
+
+def test_network_element_imbalance_rejected(oracle_mod, tmp_path):
+    net = I.robertson_network()
+    net.counts = np.array([[1], [1], [2]])
+    p = str(tmp_path / "bad.net")
+    net.write(p)
+    with pytest.raises(ValueError):
+        oracle_mod.OracleNetwork(p)
