@@ -1,0 +1,368 @@
+"""Benchmark: cell-integrations/s of the per-cell stiff thermochemistry integrator.
+
+One step = one integrate call over the whole synthetic batch of the workload (all
+cells advanced over the full dt): rates, Jacobian, LU, solve and adaptive sub-steps
+for every cell.  Default workload: the combustion-like network (10 species,
+2 elements, 30 reversible reactions, temperature equation), 65,536 cells, dt = 1e-6 s.
+
+Printed JSON line (rank 0): value = the chosen form's cells/s (FP32-LU simplified
+Newton, persistent kernel), with the plain FP64 form alongside under "forms";
+"e2e" = the same metric through kt_state upload / integrate / download with pinned
+host buffers; "roofline" = algorithmic FLOP/s of the integrate kernel against the
+FP64 pipe peak; "cpu_baseline" = the FP64 oracle on a bounded sample on the host.
+
+--impl reference times the FP64 CPU oracle itself on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2504_04941_gb300 import inputs as I  # noqa: E402
+
+METRIC = ("cell-integrations/s over fixed Δt at 1e-6 rel error vs FP64 oracle; "
+          "plain vs chosen form")
+UNIT = "cell-integrations/s"
+# FP64 pipe of GB300: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz = 1.26 TFLOP/s
+# (nominal 1.25 TFLOP/s); FP32: 152 x 128 FMA/clk x 2 x 2.07 GHz = 80.5 TFLOP/s.
+FP64_PEAK_TFLOPS = 1.25
+FP32_PEAK_TFLOPS = 80.5
+
+
+# ------------------------------------------------------------------ work counts
+
+
+def _lu_flops(N: int) -> int:
+    f = 0
+    for j in range(N):
+        for i in range(N):
+            f += 2 * min(i, j)
+        f += N - 1 - j           # scale the L column by the inverse pivot
+    return f
+
+
+def flops_per_newton(net: I.Network, form: int):
+    """(fp64 flops, fp32 flops per factorisation, transcendentals) of one Newton
+    iteration, counting each multiply and add once (an FMA as 2)."""
+    N = net.n
+    rates = fp64 = fp32 = 0
+    for ins, outs in zip(net.reac_in, net.reac_out):
+        nin, nout = len(ins), len(outs)
+        r64 = (7 if net.energy else 0) + nin + (nin + nout) + (2 if net.energy else 0)
+        jac = nin * (nin + (nin + nout) + (2 if net.energy else 0))
+        if net.energy:
+            jac += (nin + 2) + (nin + nout) + 2
+        fp64 += r64
+        if form == 0:
+            fp64 += jac
+        else:
+            fp32 += jac
+        rates += 1 if net.energy else 0
+    lu, solve = _lu_flops(N), 2 * N * N - N
+    if form == 0:
+        fp64 += N + lu + solve + 3 * N + 3 * N
+    else:
+        fp64 += 3 * N + 3 * N
+        fp32 += 2 * N * N + lu + solve
+    return fp64, fp32, rates
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms in the background."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+                power.append(float(p[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ CPU oracle legs
+
+
+def oracle_time(wl: I.Workload, ncells: int, seed_offset: int = 0):
+    """Time the FP64 oracle (as it stands) on the first ``ncells`` cells of a fresh
+    draw of the workload; returns (cells/s, threads, wall seconds)."""
+    from oracle import oracle
+    sub = I.workload(wl.wid, ncells, seed=I.SEED_BASE + wl.wid + seed_offset).cells
+    net = oracle.OracleNetwork(wl.network)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = net.integrate(sub, wl.tol.dt, oracle.options(wl.tol), threads)
+    wall = time.perf_counter() - t0
+    assert np.all(r["status"] <= 1)
+    return ncells / wall, threads, wall
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    wl = I.workload(args.workload, 1)
+    n = args.ref_cells
+    times = []
+    for s in range(args.warmup + args.steps):
+        v, threads, wall = oracle_time(wl, n, seed_offset=0)
+        if s >= args.warmup:
+            times.append(wall)
+    value = n * len(times) / sum(times)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args, wl, n),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"{n} cells of the {wl.name} workload per step (same "
+                                       f"network, tolerances and dt), pthreads over cells"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(args, wl: I.Workload, ncells: int) -> dict:
+    t = wl.tol
+    return {"workload": f"{wl.name}: {wl.network.ns} species / {wl.network.ne} elements / "
+                        f"{wl.network.nr} directed reactions"
+                        f"{' + temperature' if wl.network.energy else ''}, {ncells} cells, "
+                        f"dt={t.dt:g} s, rtol={t.rtol:g}, atol={t.atol:g}",
+            "ncells": ncells, "dt": t.dt, "rtol": t.rtol, "atol": t.atol,
+            "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": f"cells sharded over {args.gpus} GPU(s), no collective"}
+
+
+# ------------------------------------------------------------------ GPU arm
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", type=int, default=2)
+    ap.add_argument("--ncells", type=int, default=None)
+    ap.add_argument("--forms", default="plain,chosen")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-cells", type=int, default=1024)
+    ap.add_argument("--ref-cells", type=int, default=512)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2504_04941_gb300 import kt
+
+    wl0 = I.workload(args.workload, 1)
+    ncells = args.ncells or I.FULL_CELLS[args.workload]
+    # weak scaling: every rank integrates its own full batch (rank-dependent seed)
+    wl = I.workload(args.workload, ncells, seed=I.SEED_BASE + args.workload + 1000 * rank)
+    net = kt.Network(wl.network)
+    dev = torch.device("cuda", local)
+    y_in = torch.from_numpy(wl.cells.y).to(dev)
+    T_in = torch.from_numpy(wl.cells.T).to(dev)
+    rho = torch.from_numpy(wl.cells.rho).to(dev)
+    out = dict(y=torch.empty_like(y_in), T=torch.empty_like(T_in),
+               status=torch.empty(ncells, dtype=torch.int32, device=dev),
+               nsub=torch.empty(ncells, dtype=torch.int32, device=dev),
+               nnewton=torch.empty(ncells, dtype=torch.int32, device=dev))
+    scratch = torch.zeros(kt.scratch_bytes(), dtype=torch.uint8, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    forms = {"plain": dict(form=kt.KT_FORM_FP64, persistent=0),
+             "chosen": dict(form=kt.KT_FORM_FP32LU, persistent=1)}
+    results = {}
+    clocks = ClockSampler(local)
+    clock_started = False
+    for name in [f for f in args.forms.split(",") if f]:
+        opts = kt.options(wl.tol, **forms[name])
+        for _ in range(args.warmup):
+            kt.integrate(net, y_in, T_in, wl.tol.dt, opts, rho=rho, out=out, scratch=scratch)
+        kt.check_scratch(scratch)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        if name == "chosen" and not clock_started:
+            clocks.start()
+            clock_started = True
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in range(args.steps):
+            flush.fill_(s & 0xff)
+            ev[s][0].record(stream)
+            kt.integrate(net, y_in, T_in, wl.tol.dt, opts, rho=rho, out=out, scratch=scratch)
+            ev[s][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        step_ms = [a.elapsed_time(b) for a, b in ev]
+        kt.check_scratch(scratch)
+        tot_ms = sum(step_ms)
+        if world > 1:
+            t = torch.tensor([tot_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            tot_ms = float(t.item())
+        nnew = out["nnewton"].to(torch.int64).sum().item()
+        nsub = out["nsub"].to(torch.int64).sum().item()
+        st = out["status"].cpu().numpy()
+        f64, f32, trans = flops_per_newton(wl.network, forms[name]["form"])
+        # factorisations: count one per Newton solve start and per refresh (upper bound
+        # of the FP32 work is not needed; the FP64 work is per iteration)
+        per_launch_ms = tot_ms / args.steps
+        results[name] = {
+            "value": world * ncells * args.steps / (tot_ms / 1e3),
+            "ms_per_step": per_launch_ms,
+            "wall_s": wall,
+            "newton_iters": int(nnew), "substeps": int(nsub),
+            "status_counts": {int(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
+            "fp64_flops_per_launch": float(nnew) * f64,
+            "fp64_tflops": float(nnew) * f64 / (per_launch_ms / 1e3) / 1e12,
+            "exp_per_s": float(nnew) * trans / (per_launch_ms / 1e3),
+            "fp32_flops_per_factorisation": f32,
+        }
+    clk = clocks.stop() if clock_started else {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+
+    head = results.get("chosen") or results.get("plain")
+    head_name = "chosen" if "chosen" in results else "plain"
+
+    # ---- end to end through the public C-ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        opts = kt.options(wl.tol, **forms[head_name])
+        hy = torch.from_numpy(wl.cells.y).pin_memory().numpy()
+        hT = torch.from_numpy(wl.cells.T).pin_memory().numpy()
+        hr = torch.from_numpy(wl.cells.rho).pin_memory().numpy()
+        ho = dict(y=torch.empty(tuple(hy.shape), dtype=torch.float64).pin_memory().numpy(),
+                  T=torch.empty(ncells, dtype=torch.float64).pin_memory().numpy(),
+                  status=torch.empty(ncells, dtype=torch.int32).pin_memory().numpy(),
+                  nsub=torch.empty(ncells, dtype=torch.int32).pin_memory().numpy(),
+                  nnewton=torch.empty(ncells, dtype=torch.int32).pin_memory().numpy())
+        state = kt.State(net, ncells)
+        state.upload(hy, hT, hr)
+        state.integrate(wl.tol.dt, opts)
+        state.download(out=ho)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            state.upload(hy, hT, hr)
+            state.integrate(wl.tol.dt, opts)
+            state.download(out=ho)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        ns = wl.network.ns
+        e2e = {"value": world * ncells * args.steps / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": ncells * (ns + 2) * 8,
+               "d2h_bytes_per_step": ncells * (ns + 1) * 8 + 3 * ncells * 4}
+        del state
+
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, threads, wall = oracle_time(wl0, args.cpu_cells)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first {args.cpu_cells} cells of a fresh draw of the {wl.name} "
+                         f"workload, full dt, {wall:.1f} s wall"}
+
+    if rank == 0:
+        r = head
+        roof = {"bound": "alu", "achieved": r["fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": r["fp64_tflops"] / FP64_PEAK_TFLOPS, "traffic": None,
+                "pipe": "fp64", "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz "
+                                               "(nominal 1.25 TFLOP/s)",
+                "kernel": f"lane_kernel ({head_name} form)"}
+        line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if head_name == "plain" else "f64+f32",
+                "data": "synthetic", "config": config_of(args, wl, ncells),
+                "forms": results, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": args.steps, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

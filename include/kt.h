@@ -1,0 +1,168 @@
+/*
+ * kt.h -- C ABI of the GB300 (sm_103a) per-cell stiff thermochemistry integrator.
+ *
+ * The operation (Wang 2025, "The Kratos Framework ...", Sec. 2.2-2.3): every cell
+ * carries species densities n^s (and, when the network has the energy equation, its
+ * temperature T) and is advanced independently over a time dt by an implicit
+ * ("semi-implicit", Sec. 2.2) solver with adaptive sub-steps.  Each Newton
+ * iteration evaluates the modified-Arrhenius rates (Sec. 2.2.1), assembles the dense
+ * species-and-temperature Jacobian (Eq. method-jacobian), LU-factorises the iteration
+ * matrix with Crout's scaled row pivoting (Algorithm lu-decomp) and solves it.  The
+ * result is post-processed (Sec. 2.2.3): negative densities are clipped and the
+ * element totals of the initial state restored; failed cells are retried with a
+ * smaller first step and reverted to their input if they fail again.
+ *
+ * Conventions
+ *   - Every function returns 0 (KT_OK) or a negative KT_E* code; the message of the
+ *     last failure on the calling thread is kt_last_error().
+ *   - Cell arrays are structure-of-arrays: y[s * ncells + c] for species s of cell c,
+ *     T[c], rho[c], all float64; status / counters are int32.
+ *   - Device pointers must stay valid until the work on `stream` has reached them;
+ *     streams are borrowed (a cudaStream_t cast to void*, NULL = legacy default).
+ *   - Calls that take a stream are asynchronous unless stated otherwise.
+ *   - Per-cell numerical failures are not call errors: they are reported in status[].
+ */
+#ifndef KT_H
+#define KT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define KT_API __attribute__((visibility("default")))
+#else
+#define KT_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define KT_OK 0
+#define KT_EINVAL (-1)    /* bad argument */
+#define KT_ENOMEM (-2)    /* host or device allocation failed */
+#define KT_ECUDA (-3)     /* a CUDA runtime call failed */
+#define KT_EPARSE (-4)    /* network file unreadable or malformed */
+#define KT_ENETWORK (-5)  /* a reaction does not conserve every element */
+#define KT_ETIMEOUT (-6)  /* a bounded device wait (TMA barrier) gave up */
+#define KT_EUNSUPPORTED (-7) /* network size beyond what the kernels are built for */
+
+/* per-cell status */
+#define KT_STATUS_OK 0
+#define KT_STATUS_RETRIED 1      /* first attempt failed, the retry succeeded */
+#define KT_STATUS_REVERTED 2     /* both attempts failed: state reverted to the input */
+#define KT_STATUS_NONFINITE 3    /* NaN / Inf in the input: cell left untouched */
+
+/* forms of the iteration */
+#define KT_FORM_FP64 0     /* full Newton, FP64 Jacobian and LU (the plain form) */
+#define KT_FORM_FP32LU 1   /* simplified Newton: FP32 Jacobian + LU, FP64 residual/update */
+
+/* Newton starting iterate */
+#define KT_GUESS_PREV 0    /* the state at the start of the step (plain predictor) */
+#define KT_GUESS_MLP 1     /* learned initial guess (needs kt_mlp_load) */
+
+typedef struct kt_network kt_network;
+typedef struct kt_state kt_state;
+
+/* Integration options.  Fill with kt_options_default() and override fields.
+ * Sub-step control: one backward-Euler step of h and two of h/2 per attempt; the
+ * weighted RMS of their difference with weights atol_i + rtol*max(|y_i|,|y2_i|)
+ * must be <= 1; the next h is h*min(facmax, max(0.2, 0.9/sqrt(err))).  Newton on
+ * each step stops when every |delta_i| <= newton_atol_frac*atol_i + newton_rtol*|y_i|
+ * (temperature: newton_rtol*|T|) and fails after max_newton iterations (h halves). */
+typedef struct {
+    double rtol;             /* relative error weight                          (1e-6) */
+    double atol;             /* absolute error weight of every species         (1e-10) */
+    double h_init;           /* first trial sub-step [s]                       (1e-6) */
+    double h_min;            /* a sub-step below this fails the attempt [s]    (1e-30) */
+    double newton_rtol;      /* Newton relative tolerance                      (1e-12) */
+    double newton_atol_frac; /* Newton absolute tolerance as a fraction of atol (1e-2) */
+    double facmax;           /* largest step growth per accepted step           (4) */
+    double retry_h_factor;   /* retry's first step = h_init * retry_h_factor   (1e-3) */
+    double retry_facmax;     /* retry's facmax                                  (2) */
+    int max_substeps;        /* attempts (accepted + rejected) per integration (100000) */
+    int max_newton;          /* Newton iterations per factorisation            (8) */
+    int form;                /* KT_FORM_*                                       (FP64) */
+    int guess;               /* KT_GUESS_*                                      (PREV) */
+    int persistent;          /* 1: persistent kernel pulling cells from a device
+                                work queue; 0: one cell per lane, one pass     (0) */
+    int retry;               /* 1: retry failed cells once                      (1) */
+    int atol_mode;           /* 0: atol absolute; 1: atol times the cell's
+                                initial total of element 0                     (0) */
+    int block_warps;         /* warps per block, 0 = automatic                   (0) */
+    int blocks_per_sm;       /* persistent grid = blocks_per_sm x SMs, 0 = automatic (0) */
+    int use_graph;           /* 1: kt_integrate replays a captured CUDA graph    (0) */
+    int reserved[6];
+} kt_options;
+
+/* Defaults listed above. */
+KT_API int kt_options_default(kt_options *opts);
+
+/* Load a reaction network from the plain-text format written by the package's
+ * input generators ("kratos_network 1" header, species with molar mass, heat of
+ * formation, heat capacity and element counts, reactions with up to three reactants
+ * and products and modified-Arrhenius A, b, theta: k = A (T/t_ref)^b exp(-theta/T),
+ * Sec. 2.2.1).  Every reaction must conserve every element (Eq. method-const-elem),
+ * else KT_ENETWORK.  The caller owns *out and frees it with kt_network_free. */
+KT_API int kt_network_load(const char *path, kt_network **out);
+
+/* Sizes of a loaded network.  Any output pointer may be NULL. */
+KT_API int kt_network_info(const kt_network *net, int *n_species, int *n_elements,
+                    int *n_reactions, int *has_temperature);
+
+KT_API void kt_network_free(kt_network *net);
+
+/* Device state for ncells cells on the current CUDA device: y [n_species][ncells],
+ * T, rho, status, counters, plus the scratch of the integrate call.  The library owns
+ * every buffer; free with kt_state_free.  ncells may be 0. */
+KT_API int kt_state_create(const kt_network *net, int64_t ncells, kt_state **out);
+
+/* Copy cell data into the state (host or device source, SoA float64).  rho may be
+ * NULL (then 1).  Asynchronous on stream; host sources must stay valid until the
+ * copy has run (pinned memory makes the copy truly asynchronous). */
+KT_API int kt_state_upload(kt_state *st, const double *y, const double *T, const double *rho,
+                    int src_is_device, void *cuda_stream);
+
+/* Advance every cell of the state by dt in place (asynchronous on stream). */
+KT_API int kt_integrate(kt_state *st, double dt, const kt_options *opts, void *cuda_stream);
+
+/* Copy results out (host or device destination).  Any output pointer may be NULL.
+ * With a host destination the call synchronises the stream and also reports a device
+ * error recorded by the integrate kernels (KT_ETIMEOUT). */
+KT_API int kt_state_download(const kt_state *st, double *y, double *T, int32_t *status,
+                      int32_t *n_substeps, int32_t *n_newton, int dst_is_device,
+                      void *cuda_stream);
+
+/* Synchronise the stream and report a device error recorded by the kernels. */
+KT_API int kt_state_check(const kt_state *st, void *cuda_stream);
+
+KT_API void kt_state_free(kt_state *st);
+
+/* Bytes of device scratch one kt_integrate_ptrs call needs (queue counter and error
+ * word); the caller passes a zero-or-not buffer of at least this size, 16-B aligned. */
+KT_API size_t kt_scratch_bytes(void);
+
+/* Same operation on caller-owned DEVICE buffers (e.g. torch tensors):
+ * y_in [n_species][ncells], T_in [ncells], rho [ncells] (may be NULL); outputs may
+ * alias the inputs (in-place integration); status/n_substeps/n_newton may be NULL.
+ * scratch: device buffer of kt_scratch_bytes() bytes, reused by the call (its
+ * content on entry does not matter).  Calls sharing a scratch buffer must be ordered
+ * on one stream. */
+KT_API int kt_integrate_ptrs(const kt_network *net, int64_t ncells, const double *y_in,
+                      const double *T_in, const double *rho, double dt,
+                      const kt_options *opts, double *y_out, double *T_out,
+                      int32_t *status, int32_t *n_substeps, int32_t *n_newton,
+                      void *scratch, void *cuda_stream);
+
+/* Read and clear the device error word of a scratch buffer (synchronises stream). */
+KT_API int kt_scratch_check(void *scratch, void *cuda_stream);
+
+/* Thread-local message of the last failed call ("" if none). */
+KT_API const char *kt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KT_H */

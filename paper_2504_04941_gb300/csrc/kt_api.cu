@@ -1,0 +1,514 @@
+// kt_api.cu -- host side of libkt: network parsing, device tables, state buffers and
+// the C entry points declared in include/kt.h.
+#include <cuda_runtime.h>
+
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "kt_internal.h"
+
+using kt::NetView;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(KT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int align16(int x) { return (x + 15) & ~15; }
+
+}  // namespace
+
+struct kt_network {
+    std::string name;
+    int ns = 0, ne = 0, nr = 0, energy = 0;
+    double t_ref = 1.0, t_min = 1.0, t_max = 1e5;
+    std::vector<double> mass, h, cv;
+    std::vector<int> counts;                      // [ns*ne]
+    std::vector<int> nin, nout;                   // [nr]
+    std::vector<std::array<int, kt::kMaxSide>> in, out;
+    std::vector<double> A, b, th;
+    std::vector<unsigned char> blob;
+    NetView view{};
+    std::mutex mu;
+    std::map<int, unsigned char *> dev_blob;      // device ordinal -> device copy
+
+    ~kt_network()
+    {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        for (auto &kv : dev_blob) {
+            cudaSetDevice(kv.first);
+            cudaFree(kv.second);
+        }
+        cudaSetDevice(cur);
+    }
+
+    // Device copy of the blob on the current device (uploaded once per device).
+    int device_blob(const unsigned char **out)
+    {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = dev_blob.find(dev);
+        if (it != dev_blob.end()) {
+            *out = it->second;
+            return KT_OK;
+        }
+        unsigned char *p = nullptr;
+        e = cudaMalloc(&p, blob.size());
+        if (e != cudaSuccess) return fail(KT_ENOMEM, "cudaMalloc(network tables): %s", cudaGetErrorString(e));
+        e = cudaMemcpy(p, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(p);
+            return cuda_fail(e, "cudaMemcpy(network tables)");
+        }
+        dev_blob[dev] = p;
+        *out = p;
+        return KT_OK;
+    }
+};
+
+struct kt_state {
+    const kt_network *net = nullptr;
+    long long ncells = 0;
+    int device = 0;
+    double *y = nullptr, *T = nullptr, *rho = nullptr;
+    int *status = nullptr, *nsub = nullptr, *nnew = nullptr;
+    kt::Scratch *scratch = nullptr;
+};
+
+namespace {
+
+// ---------------------------------------------------------------- network file parser
+
+struct Tok {
+    std::istringstream in;
+    explicit Tok(const std::string &s) : in(s) {}
+    bool next(std::string &w) { return static_cast<bool>(in >> w); }
+    bool word(const char *expect)
+    {
+        std::string w;
+        return next(w) && w == expect;
+    }
+    bool integer(int &v)
+    {
+        std::string w;
+        if (!next(w)) return false;
+        char *end = nullptr;
+        long x = std::strtol(w.c_str(), &end, 10);
+        if (*end) return false;
+        v = static_cast<int>(x);
+        return true;
+    }
+    bool real(double &v)
+    {
+        std::string w;
+        if (!next(w)) return false;
+        char *end = nullptr;
+        v = std::strtod(w.c_str(), &end);
+        return *end == 0;
+    }
+};
+
+std::string strip_comments(std::istream &f)
+{
+    std::string out, line;
+    while (std::getline(f, line)) {
+        auto p = line.find('#');
+        if (p != std::string::npos) line.resize(p);
+        out += line;
+        out += '\n';
+    }
+    return out;
+}
+
+int parse_network(const std::string &text, kt_network *n)
+{
+    Tok t(text);
+    int version = 0;
+    std::string w;
+    if (!(t.word("kratos_network") && t.integer(version) && version == 1))
+        return fail(KT_EPARSE, "network: missing 'kratos_network 1' header");
+    if (!(t.word("name") && t.next(n->name) && t.word("n_species") && t.integer(n->ns) &&
+          t.word("n_elements") && t.integer(n->ne) && t.word("n_reactions") && t.integer(n->nr) &&
+          t.word("energy") && t.integer(n->energy) && t.word("t_ref") && t.real(n->t_ref) &&
+          t.word("t_min") && t.real(n->t_min) && t.word("t_max") && t.real(n->t_max) &&
+          t.word("elements")))
+        return fail(KT_EPARSE, "network: malformed header");
+    if (n->ns < 1 || n->ns > 250 || n->ne < 1 || n->ne > kt::kMaxElements || n->nr < 0 ||
+        (n->energy != 0 && n->energy != 1) || !(n->t_ref > 0) || !(n->t_min > 0) || !(n->t_max >= n->t_min))
+        return fail(KT_EPARSE, "network: sizes or limits out of range");
+    for (int e = 0; e < n->ne; ++e)
+        if (!t.next(w)) return fail(KT_EPARSE, "network: element names");
+    n->mass.resize(n->ns);
+    n->h.resize(n->ns);
+    n->cv.resize(n->ns);
+    n->counts.resize(static_cast<size_t>(n->ns) * n->ne);
+    for (int s = 0; s < n->ns; ++s) {
+        if (!(t.word("species") && t.next(w) && t.real(n->mass[s]) && t.real(n->h[s]) && t.real(n->cv[s])))
+            return fail(KT_EPARSE, "network: species line %d", s);
+        for (int e = 0; e < n->ne; ++e)
+            if (!t.integer(n->counts[s * n->ne + e])) return fail(KT_EPARSE, "network: species %d counts", s);
+    }
+    n->nin.resize(n->nr);
+    n->nout.resize(n->nr);
+    n->in.resize(n->nr);
+    n->out.resize(n->nr);
+    n->A.resize(n->nr);
+    n->b.resize(n->nr);
+    n->th.resize(n->nr);
+    for (int r = 0; r < n->nr; ++r) {
+        int pair = 0;
+        n->in[r].fill(-1);
+        n->out[r].fill(-1);
+        if (!(t.word("reaction") && t.integer(n->nin[r]) && n->nin[r] >= 1 && n->nin[r] <= kt::kMaxSide))
+            return fail(KT_EPARSE, "network: reaction %d reactants", r);
+        for (int j = 0; j < n->nin[r]; ++j)
+            if (!(t.integer(n->in[r][j]) && n->in[r][j] >= 0 && n->in[r][j] < n->ns))
+                return fail(KT_EPARSE, "network: reaction %d reactant index", r);
+        if (!(t.integer(n->nout[r]) && n->nout[r] >= 0 && n->nout[r] <= kt::kMaxSide))
+            return fail(KT_EPARSE, "network: reaction %d products", r);
+        for (int j = 0; j < n->nout[r]; ++j)
+            if (!(t.integer(n->out[r][j]) && n->out[r][j] >= 0 && n->out[r][j] < n->ns))
+                return fail(KT_EPARSE, "network: reaction %d product index", r);
+        if (!(t.real(n->A[r]) && t.real(n->b[r]) && t.real(n->th[r]) && t.integer(pair)))
+            return fail(KT_EPARSE, "network: reaction %d parameters", r);
+    }
+    if (!t.word("end")) return fail(KT_EPARSE, "network: missing 'end'");
+    // element conservation of every reaction (Eq. method-const-elem)
+    for (int r = 0; r < n->nr; ++r)
+        for (int e = 0; e < n->ne; ++e) {
+            int bal = 0;
+            for (int j = 0; j < n->nin[r]; ++j) bal -= n->counts[n->in[r][j] * n->ne + e];
+            for (int j = 0; j < n->nout[r]; ++j) bal += n->counts[n->out[r][j] * n->ne + e];
+            if (bal != 0) return fail(KT_ENETWORK, "network: reaction %d does not conserve element %d", r, e);
+        }
+    return KT_OK;
+}
+
+// Pack the device tables (layout kt::NetView).
+void build_blob(kt_network *n)
+{
+    NetView &v = n->view;
+    v.ns = n->ns;
+    v.ne = n->ne;
+    v.nr = n->nr;
+    v.energy = n->energy;
+    v.N = n->ns + n->energy;
+    v.t_ref = n->t_ref;
+    v.t_min = n->t_min;
+    v.t_max = n->t_max;
+    int o = 0;
+    v.off_A = o; o = align16(o + 8 * n->nr);
+    v.off_b = o; o = align16(o + 8 * n->nr);
+    v.off_th = o; o = align16(o + 8 * n->nr);
+    v.off_dH = o; o = align16(o + 8 * n->nr);
+    v.off_h = o; o = align16(o + 8 * n->ns);
+    v.off_cv = o; o = align16(o + 8 * n->ns);
+    v.off_cnt = o; o = align16(o + 8 * n->ns * n->ne);
+    v.off_idx = o; o = align16(o + 8 * n->nr);
+    if (o < 16) o = 16;
+    v.bytes = o;
+    n->blob.assign(o, 0);
+    auto put = [&](int off, int i, double x) { std::memcpy(n->blob.data() + off + 8 * i, &x, 8); };
+    for (int r = 0; r < n->nr; ++r) {
+        put(v.off_A, r, n->A[r]);
+        put(v.off_b, r, n->b[r]);
+        put(v.off_th, r, n->th[r]);
+        double dH = 0.0;
+        for (int j = 0; j < n->nout[r]; ++j) dH += n->h[n->out[r][j]];
+        for (int j = 0; j < n->nin[r]; ++j) dH -= n->h[n->in[r][j]];
+        put(v.off_dH, r, dH);
+        unsigned char *ix = n->blob.data() + v.off_idx + 8 * r;
+        ix[0] = static_cast<unsigned char>(n->nin[r]);
+        ix[1] = static_cast<unsigned char>(n->nout[r]);
+        for (int j = 0; j < kt::kMaxSide; ++j) {
+            ix[2 + j] = static_cast<unsigned char>(j < n->nin[r] ? n->in[r][j] : kt::kIdxNone);
+            ix[5 + j] = static_cast<unsigned char>(j < n->nout[r] ? n->out[r][j] : kt::kIdxNone);
+        }
+    }
+    for (int s = 0; s < n->ns; ++s) {
+        put(v.off_h, s, n->h[s]);
+        put(v.off_cv, s, n->cv[s]);
+        for (int e = 0; e < n->ne; ++e) put(v.off_cnt, s * n->ne + e, static_cast<double>(n->counts[s * n->ne + e]));
+    }
+}
+
+int check_opts(const kt_options *o)
+{
+    if (!o) return fail(KT_EINVAL, "options: NULL");
+    if (!(o->rtol > 0) || !(o->atol > 0) || !(o->h_init > 0) || !(o->h_min >= 0) ||
+        !(o->newton_rtol > 0) || !(o->newton_atol_frac > 0) || !(o->facmax >= 1) ||
+        !(o->retry_h_factor > 0) || !(o->retry_facmax >= 1) || o->max_substeps < 1 ||
+        o->max_newton < 1 || (o->form != KT_FORM_FP64 && o->form != KT_FORM_FP32LU) ||
+        (o->guess != KT_GUESS_PREV && o->guess != KT_GUESS_MLP) || o->block_warps < 0 ||
+        o->blocks_per_sm < 0)
+        return fail(KT_EINVAL, "options: a field is out of range");
+    if (o->guess == KT_GUESS_MLP) return fail(KT_EUNSUPPORTED, "options: learned guess needs kt_mlp_load");
+    return KT_OK;
+}
+
+kt::DevOpts dev_opts(const kt_options *o)
+{
+    kt::DevOpts d{};
+    d.rtol = o->rtol;
+    d.atol = o->atol;
+    d.h_init = o->h_init;
+    d.h_min = o->h_min;
+    d.newton_rtol = o->newton_rtol;
+    d.newton_atol_frac = o->newton_atol_frac;
+    d.facmax = o->facmax;
+    d.retry_h_factor = o->retry_h_factor;
+    d.retry_facmax = o->retry_facmax;
+    d.max_substeps = o->max_substeps;
+    d.max_newton = o->max_newton;
+    d.retry = o->retry;
+    d.atol_mode = o->atol_mode;
+    d.guess = o->guess;
+    return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *kt_last_error(void) { return g_err.c_str(); }
+
+int kt_options_default(kt_options *o)
+{
+    if (!o) return fail(KT_EINVAL, "kt_options_default: NULL");
+    std::memset(o, 0, sizeof *o);
+    o->rtol = 1e-6;
+    o->atol = 1e-10;
+    o->h_init = 1e-6;
+    o->h_min = 1e-30;
+    o->newton_rtol = 1e-12;
+    o->newton_atol_frac = 1e-2;
+    o->facmax = 4.0;
+    o->retry_h_factor = 1e-3;
+    o->retry_facmax = 2.0;
+    o->max_substeps = 100000;
+    o->max_newton = 8;
+    o->form = KT_FORM_FP64;
+    o->guess = KT_GUESS_PREV;
+    o->persistent = 0;
+    o->retry = 1;
+    o->atol_mode = 0;
+    return KT_OK;
+}
+
+int kt_network_load(const char *path, kt_network **out)
+{
+    if (!path || !out) return fail(KT_EINVAL, "kt_network_load: NULL argument");
+    *out = nullptr;
+    std::ifstream f(path);
+    if (!f) return fail(KT_EPARSE, "kt_network_load: cannot open %s", path);
+    kt_network *n = new (std::nothrow) kt_network();
+    if (!n) return fail(KT_ENOMEM, "kt_network_load: out of memory");
+    int rc = parse_network(strip_comments(f), n);
+    if (rc != KT_OK) {
+        delete n;
+        return rc;
+    }
+    build_blob(n);
+    *out = n;
+    return KT_OK;
+}
+
+int kt_network_info(const kt_network *n, int *ns, int *ne, int *nr, int *energy)
+{
+    if (!n) return fail(KT_EINVAL, "kt_network_info: NULL network");
+    if (ns) *ns = n->ns;
+    if (ne) *ne = n->ne;
+    if (nr) *nr = n->nr;
+    if (energy) *energy = n->energy;
+    return KT_OK;
+}
+
+void kt_network_free(kt_network *n) { delete n; }
+
+size_t kt_scratch_bytes(void) { return sizeof(kt::Scratch); }
+
+int kt_integrate_ptrs(const kt_network *net, int64_t ncells, const double *y_in, const double *T_in,
+                      const double *rho, double dt, const kt_options *opts, double *y_out,
+                      double *T_out, int32_t *status, int32_t *n_substeps, int32_t *n_newton,
+                      void *scratch, void *cuda_stream)
+{
+    (void)rho;
+    if (!net) return fail(KT_EINVAL, "kt_integrate_ptrs: NULL network");
+    if (ncells < 0 || !(dt > 0) || !std::isfinite(dt)) return fail(KT_EINVAL, "kt_integrate_ptrs: bad ncells or dt");
+    int rc = check_opts(opts);
+    if (rc) return rc;
+    if (ncells == 0) return KT_OK;
+    if (!y_in || !T_in || !y_out || !T_out || !scratch)
+        return fail(KT_EINVAL, "kt_integrate_ptrs: NULL device buffer");
+    if (reinterpret_cast<uintptr_t>(scratch) % 16) return fail(KT_EINVAL, "kt_integrate_ptrs: scratch not 16-B aligned");
+    const int N = net->ns + net->energy;
+    if (N > kt::kLaneMaxN)
+        return fail(KT_EUNSUPPORTED, "kt_integrate_ptrs: %d unknowns per cell; this build handles up to %d", N,
+                    kt::kLaneMaxN);
+    kt_network *mn = const_cast<kt_network *>(net);
+    const unsigned char *blob = nullptr;
+    rc = mn->device_blob(&blob);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(kt::Scratch), s);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(scratch)");
+    kt::LaunchArgs a{};
+    a.nv = net->view;
+    a.blob = blob;
+    a.o = dev_opts(opts);
+    a.dt = dt;
+    a.ncells = ncells;
+    a.y_in = y_in;
+    a.T_in = T_in;
+    a.y_out = y_out;
+    a.T_out = T_out;
+    a.status = status;
+    a.nsub = n_substeps;
+    a.nnew = n_newton;
+    a.scratch = static_cast<kt::Scratch *>(scratch);
+    kt::LaunchCfg c{opts->form, opts->persistent, opts->block_warps, opts->blocks_per_sm};
+    int ce = kt::launch_lane(a, c, cuda_stream);
+    if (ce != 0) return cuda_fail(static_cast<cudaError_t>(ce), "integrate kernel launch");
+    return KT_OK;
+}
+
+int kt_scratch_check(void *scratch, void *cuda_stream)
+{
+    if (!scratch) return fail(KT_EINVAL, "kt_scratch_check: NULL scratch");
+    kt::Scratch h{};
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaMemcpyAsync(&h, scratch, sizeof h, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "kt_scratch_check");
+    if (h.error != 0) {
+        int zero = 0;
+        cudaMemcpyAsync(reinterpret_cast<char *>(scratch) + offsetof(kt::Scratch, error), &zero, sizeof zero,
+                        cudaMemcpyHostToDevice, s);
+        cudaStreamSynchronize(s);
+        return fail(KT_ETIMEOUT, "device: a bounded wait for the network-table copy gave up (code %d)", h.error);
+    }
+    return KT_OK;
+}
+
+int kt_state_create(const kt_network *net, int64_t ncells, kt_state **out)
+{
+    if (!net || !out || ncells < 0) return fail(KT_EINVAL, "kt_state_create: bad argument");
+    *out = nullptr;
+    kt_state *st = new (std::nothrow) kt_state();
+    if (!st) return fail(KT_ENOMEM, "kt_state_create: out of memory");
+    st->net = net;
+    st->ncells = ncells;
+    cudaGetDevice(&st->device);
+    const size_t n = static_cast<size_t>(ncells > 0 ? ncells : 1);
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void **p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    alloc(reinterpret_cast<void **>(&st->y), n * net->ns * sizeof(double));
+    alloc(reinterpret_cast<void **>(&st->T), n * sizeof(double));
+    alloc(reinterpret_cast<void **>(&st->rho), n * sizeof(double));
+    alloc(reinterpret_cast<void **>(&st->status), n * sizeof(int));
+    alloc(reinterpret_cast<void **>(&st->nsub), n * sizeof(int));
+    alloc(reinterpret_cast<void **>(&st->nnew), n * sizeof(int));
+    alloc(reinterpret_cast<void **>(&st->scratch), sizeof(kt::Scratch));
+    if (e == cudaSuccess) e = cudaMemset(st->scratch, 0, sizeof(kt::Scratch));
+    if (e == cudaSuccess) e = cudaMemset(st->status, 0, n * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(st->nsub, 0, n * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(st->nnew, 0, n * sizeof(int));
+    if (e != cudaSuccess) {
+        kt_state_free(st);
+        return fail(KT_ENOMEM, "kt_state_create: %s", cudaGetErrorString(e));
+    }
+    *out = st;
+    return KT_OK;
+}
+
+void kt_state_free(kt_state *st)
+{
+    if (!st) return;
+    cudaFree(st->y);
+    cudaFree(st->T);
+    cudaFree(st->rho);
+    cudaFree(st->status);
+    cudaFree(st->nsub);
+    cudaFree(st->nnew);
+    cudaFree(st->scratch);
+    delete st;
+}
+
+int kt_state_upload(kt_state *st, const double *y, const double *T, const double *rho, int src_is_device,
+                    void *cuda_stream)
+{
+    if (!st || !y || !T) return fail(KT_EINVAL, "kt_state_upload: NULL argument");
+    if (st->ncells == 0) return KT_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const cudaMemcpyKind k = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    const size_t n = static_cast<size_t>(st->ncells);
+    cudaError_t e = cudaMemcpyAsync(st->y, y, n * st->net->ns * sizeof(double), k, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(st->T, T, n * sizeof(double), k, s);
+    if (e == cudaSuccess && rho) e = cudaMemcpyAsync(st->rho, rho, n * sizeof(double), k, s);
+    if (e != cudaSuccess) return cuda_fail(e, "kt_state_upload");
+    return KT_OK;
+}
+
+int kt_integrate(kt_state *st, double dt, const kt_options *opts, void *cuda_stream)
+{
+    if (!st) return fail(KT_EINVAL, "kt_integrate: NULL state");
+    return kt_integrate_ptrs(st->net, st->ncells, st->y, st->T, st->rho, dt, opts, st->y, st->T, st->status,
+                             st->nsub, st->nnew, st->scratch, cuda_stream);
+}
+
+int kt_state_check(const kt_state *st, void *cuda_stream)
+{
+    if (!st) return fail(KT_EINVAL, "kt_state_check: NULL state");
+    return kt_scratch_check(st->scratch, cuda_stream);
+}
+
+int kt_state_download(const kt_state *st, double *y, double *T, int32_t *status, int32_t *n_substeps,
+                      int32_t *n_newton, int dst_is_device, void *cuda_stream)
+{
+    if (!st) return fail(KT_EINVAL, "kt_state_download: NULL state");
+    if (st->ncells == 0) return KT_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const cudaMemcpyKind k = dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const size_t n = static_cast<size_t>(st->ncells);
+    cudaError_t e = cudaSuccess;
+    if (y) e = cudaMemcpyAsync(y, st->y, n * st->net->ns * sizeof(double), k, s);
+    if (e == cudaSuccess && T) e = cudaMemcpyAsync(T, st->T, n * sizeof(double), k, s);
+    if (e == cudaSuccess && status) e = cudaMemcpyAsync(status, st->status, n * sizeof(int), k, s);
+    if (e == cudaSuccess && n_substeps) e = cudaMemcpyAsync(n_substeps, st->nsub, n * sizeof(int), k, s);
+    if (e == cudaSuccess && n_newton) e = cudaMemcpyAsync(n_newton, st->nnew, n * sizeof(int), k, s);
+    if (e != cudaSuccess) return cuda_fail(e, "kt_state_download");
+    if (!dst_is_device) return kt_scratch_check(st->scratch, cuda_stream);
+    return KT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,237 @@
+"""Python binding of libkt (include/kt.h): argument marshalling only.
+
+Every step of the integration runs in the CUDA library; this module only passes
+pointers, sizes and a stream.  PyTorch supplies device memory and streams.  If the
+library is missing the import of a handle fails loudly; there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import tempfile
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libkt.so")
+
+KT_FORM_FP64 = 0
+KT_FORM_FP32LU = 1
+KT_GUESS_PREV = 0
+KT_GUESS_MLP = 1
+STATUS_OK, STATUS_RETRIED, STATUS_REVERTED, STATUS_NONFINITE = 0, 1, 2, 3
+
+_lib = None
+
+
+class KtError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libkt error {code}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    """Mirror of kt_options."""
+    _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double),
+                ("h_init", ctypes.c_double), ("h_min", ctypes.c_double),
+                ("newton_rtol", ctypes.c_double), ("newton_atol_frac", ctypes.c_double),
+                ("facmax", ctypes.c_double), ("retry_h_factor", ctypes.c_double),
+                ("retry_facmax", ctypes.c_double),
+                ("max_substeps", ctypes.c_int), ("max_newton", ctypes.c_int),
+                ("form", ctypes.c_int), ("guess", ctypes.c_int), ("persistent", ctypes.c_int),
+                ("retry", ctypes.c_int), ("atol_mode", ctypes.c_int),
+                ("block_warps", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+
+
+def lib():
+    """The loaded libkt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libkt.so not built ({LIB_PATH}); run "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, c_i64, c_int = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        dptr = ctypes.c_void_p
+        L.kt_last_error.restype = ctypes.c_char_p
+        L.kt_options_default.argtypes = [ctypes.POINTER(Options)]
+        L.kt_network_load.argtypes = [ctypes.c_char_p, ctypes.POINTER(vp)]
+        L.kt_network_info.argtypes = [vp] + [ctypes.POINTER(c_int)] * 4
+        L.kt_network_free.argtypes = [vp]
+        L.kt_network_free.restype = None
+        L.kt_state_create.argtypes = [vp, c_i64, ctypes.POINTER(vp)]
+        L.kt_state_upload.argtypes = [vp, dptr, dptr, dptr, c_int, vp]
+        L.kt_integrate.argtypes = [vp, ctypes.c_double, ctypes.POINTER(Options), vp]
+        L.kt_state_download.argtypes = [vp, dptr, dptr, dptr, dptr, dptr, c_int, vp]
+        L.kt_state_check.argtypes = [vp, vp]
+        L.kt_state_free.argtypes = [vp]
+        L.kt_state_free.restype = None
+        L.kt_scratch_bytes.restype = ctypes.c_size_t
+        L.kt_integrate_ptrs.argtypes = [vp, c_i64, dptr, dptr, dptr, ctypes.c_double,
+                                        ctypes.POINTER(Options), dptr, dptr, dptr, dptr, dptr,
+                                        dptr, vp]
+        L.kt_scratch_check.argtypes = [vp, vp]
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise KtError(rc, lib().kt_last_error().decode(errors="replace"))
+
+
+def options(tol=None, **kw) -> Options:
+    """kt_options_default() plus fields of an ``inputs.Tolerances`` and overrides."""
+    o = Options()
+    _check(lib().kt_options_default(ctypes.byref(o)))
+    if tol is not None:
+        o.rtol, o.atol, o.h_init, o.h_min = tol.rtol, tol.atol, tol.h_init, tol.h_min
+        o.max_substeps, o.max_newton, o.atol_mode = tol.max_substeps, tol.max_newton, tol.atol_mode
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Network:
+    """A network loaded by libkt's parser (from a path or an ``inputs.Network``)."""
+
+    def __init__(self, net_or_path):
+        L = lib()
+        tmp = None
+        if isinstance(net_or_path, str):
+            path = net_or_path
+        else:
+            fd, path = tempfile.mkstemp(suffix=".net")
+            os.close(fd)
+            net_or_path.write(path)
+            tmp = path
+        self.ptr = ctypes.c_void_p()
+        try:
+            _check(L.kt_network_load(path.encode(), ctypes.byref(self.ptr)))
+        finally:
+            if tmp:
+                os.unlink(tmp)
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(L.kt_network_info(self.ptr, *[ctypes.byref(x) for x in v]))
+        self.ns, self.ne, self.nr, self.energy = (x.value for x in v)
+        self.n = self.ns + self.energy
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                lib().kt_network_free(self.ptr)
+                self.ptr = None
+        except Exception:
+            pass
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream_handle(stream) -> Optional[int]:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def integrate(net: Network, y, T, dt: float, opts: Options, rho=None, out=None,
+              scratch=None, stream=None):
+    """Integrate cells held in CUDA tensors (float64, y: [ns, ncells] contiguous).
+
+    Returns a dict of device tensors y, T, status, nsub, nnewton (``out`` may supply
+    them; passing y/T themselves integrates in place).  Asynchronous on ``stream``."""
+    import torch
+    ncells = T.shape[0]
+    dev = T.device
+    if out is None:
+        out = {}
+    yo = out.get("y")
+    if yo is None:
+        yo = torch.empty_like(y)
+    To = out.get("T")
+    if To is None:
+        To = torch.empty_like(T)
+    st = out.get("status")
+    if st is None:
+        st = torch.empty(ncells, dtype=torch.int32, device=dev)
+    nsub = out.get("nsub")
+    if nsub is None:
+        nsub = torch.empty(ncells, dtype=torch.int32, device=dev)
+    nnew = out.get("nnewton")
+    if nnew is None:
+        nnew = torch.empty(ncells, dtype=torch.int32, device=dev)
+    if scratch is None:
+        scratch = torch.empty(scratch_bytes(), dtype=torch.uint8, device=dev)
+    for tns in (y, T, yo, To):
+        if tns.dtype != torch.float64 or not tns.is_contiguous() or not tns.is_cuda:
+            raise ValueError("y, T and outputs must be contiguous float64 CUDA tensors")
+    _check(lib().kt_integrate_ptrs(net.ptr, ncells, _ptr(y), _ptr(T), _ptr(rho), float(dt),
+                                   ctypes.byref(opts), _ptr(yo), _ptr(To), _ptr(st), _ptr(nsub),
+                                   _ptr(nnew), _ptr(scratch), _stream_handle(stream)))
+    return dict(y=yo, T=To, status=st, nsub=nsub, nnewton=nnew, scratch=scratch)
+
+
+def scratch_bytes() -> int:
+    return int(lib().kt_scratch_bytes())
+
+
+def check_scratch(scratch, stream=None):
+    """Synchronise and raise if a kernel recorded a device error in ``scratch``."""
+    _check(lib().kt_scratch_check(_ptr(scratch), _stream_handle(stream)))
+
+
+class State:
+    """Library-owned device state (kt_state): upload, integrate in place, download."""
+
+    def __init__(self, net: Network, ncells: int):
+        self.net = net
+        self.ncells = int(ncells)
+        self.ptr = ctypes.c_void_p()
+        _check(lib().kt_state_create(net.ptr, self.ncells, ctypes.byref(self.ptr)))
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                lib().kt_state_free(self.ptr)
+                self.ptr = None
+        except Exception:
+            pass
+
+    def upload(self, y, T, rho=None, stream=None):
+        """y, T, rho: numpy arrays (host) or CUDA tensors (device)."""
+        dev = hasattr(y, "data_ptr") and getattr(y, "is_cuda", False)
+        if dev:
+            args = (_ptr(y), _ptr(T), _ptr(rho))
+        else:
+            args = (_np_ptr(y), _np_ptr(T), _np_ptr(rho))
+        _check(lib().kt_state_upload(self.ptr, *args, int(dev), _stream_handle(stream)))
+
+    def integrate(self, dt: float, opts: Options, stream=None):
+        _check(lib().kt_integrate(self.ptr, float(dt), ctypes.byref(opts), _stream_handle(stream)))
+
+    def download(self, stream=None, out=None):
+        """Copy results into host numpy arrays (synchronises; raises on device errors)."""
+        ns, nc = self.net.ns, self.ncells
+        if out is None:
+            out = dict(y=np.empty((ns, nc)), T=np.empty(nc), status=np.empty(nc, np.int32),
+                       nsub=np.empty(nc, np.int32), nnewton=np.empty(nc, np.int32))
+        _check(lib().kt_state_download(self.ptr, _np_ptr(out["y"]), _np_ptr(out["T"]),
+                                       _np_ptr(out["status"]), _np_ptr(out["nsub"]),
+                                       _np_ptr(out["nnewton"]), 0, _stream_handle(stream)))
+        return out
+
+    def check(self, stream=None):
+        _check(lib().kt_state_check(self.ptr, _stream_handle(stream)))
+
+
+def _np_ptr(a) -> Optional[int]:
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("host arrays must be C-contiguous")
+    return a.ctypes.data

@@ -1,0 +1,163 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C-ABI.
+
+Sizes: the Robertson workload at full size (1024 cells, several warps and blocks),
+the combustion network on a ragged 250-cell batch (not a multiple of 32), and the
+full 65,536-cell combustion workload in the benchmark's launch configuration with
+the oracle on sampled cells.  Edge cases: empty and single-cell batches, non-finite
+inputs, negative inputs, forced reverts, split ranges (bit-identical) and repeat
+runs (bit-identical).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2504_04941_gb300 import inputs as I
+from _parity import compare, conservation_error
+
+pytestmark = pytest.mark.gpu
+
+NTHREADS = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def kt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_04941_gb300 import build, kt as ktm
+    build.build()
+    return ktm
+
+
+def gpu_run(kt, net_py, cells, dt, opts, net=None):
+    import torch
+    net = net or kt.Network(net_py)
+    y = torch.from_numpy(np.ascontiguousarray(cells.y)).cuda()
+    T = torch.from_numpy(np.ascontiguousarray(cells.T)).cuda()
+    r = kt.integrate(net, y, T, dt, opts)
+    kt.check_scratch(r["scratch"])
+    torch.cuda.synchronize()
+    return {k: r[k].cpu().numpy() for k in ("y", "T", "status", "nsub", "nnewton")}
+
+
+def ora_run(oracle_mod, net_py, cells, dt, tol, **kw):
+    net = oracle_mod.OracleNetwork(net_py)
+    return net.integrate(cells, dt, oracle_mod.options(tol, **kw), NTHREADS)
+
+
+FORMS = [dict(form=0, persistent=0), dict(form=0, persistent=1), dict(form=1, persistent=1)]
+
+
+@pytest.mark.parametrize("form", FORMS, ids=["fp64", "fp64-persistent", "fp32lu-persistent"])
+def test_robertson_full_parity(kt, oracle_mod, form):
+    wl = I.workload(1)
+    g = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, kt.options(wl.tol, **form))
+    o = ora_run(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol)
+    rep = compare(g, o, wl.network.energy)
+    print(rep)
+    assert rep.ok(), rep
+    assert conservation_error(wl.network, wl.cells.y, g["y"]) <= 1e-12
+    if form["form"] == 0:
+        assert rep.n_flip == 0
+        assert np.array_equal(g["nnewton"], o["nnewton"])
+
+
+@pytest.mark.parametrize("form", FORMS, ids=["fp64", "fp64-persistent", "fp32lu-persistent"])
+def test_combustion_ragged_parity(kt, oracle_mod, form):
+    wl = I.workload(2, 250)
+    g = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, kt.options(wl.tol, **form))
+    o = ora_run(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol)
+    rep = compare(g, o, wl.network.energy)
+    print(rep)
+    assert rep.ok(), rep
+    assert conservation_error(wl.network, wl.cells.y, g["y"]) <= 1e-12
+    assert np.all(g["y"] >= 0)
+    # energy invariant C_V T + sum h y of the pre-processed state
+    net = wl.network
+    y0 = np.maximum(wl.cells.y, 0)
+    cv = net.cv @ y0
+    E0 = cv * wl.cells.T + net.h @ y0
+    E1 = cv * g["T"] + net.h @ g["y"]
+    assert np.all(np.abs(E1 - E0) <= 1e-11 * (cv * wl.cells.T + np.abs(net.h) @ y0))
+
+
+@pytest.mark.parametrize("form", [0, 1], ids=["fp64", "fp32lu"])
+def test_combustion_full_size_sampled(kt, oracle_mod, form):
+    """Full 65,536-cell workload, persistent launch as benchmarked; 48 sampled cells."""
+    wl = I.workload(2)
+    g = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, kt.options(wl.tol, form=form, persistent=1))
+    assert np.all(g["status"] == 0)
+    rng = np.random.default_rng(11)
+    idx = np.sort(rng.choice(wl.cells.ncells, 48, replace=False))
+    sub = wl.cells.subset(idx)
+    o = ora_run(oracle_mod, wl.network, sub, wl.tol.dt, wl.tol)
+    gs = {k: (v[:, idx] if v.ndim == 2 else v[idx]) for k, v in g.items()}
+    rep = compare(gs, o, wl.network.energy)
+    print(rep)
+    assert rep.ok(max_flip_frac=0.05), rep
+    assert conservation_error(wl.network, wl.cells.y, g["y"]) <= 1e-12
+
+
+def test_edge_cases(kt, oracle_mod):
+    import torch
+    wl = I.workload(1, 40)
+    net = kt.Network(wl.network)
+    opts = kt.options(wl.tol)
+    # empty batch: no-op
+    y = torch.zeros((3, 0), dtype=torch.float64, device="cuda")
+    T = torch.zeros(0, dtype=torch.float64, device="cuda")
+    r = kt.integrate(net, y, T, 1.0, opts)
+    assert r["y"].shape == (3, 0)
+    # one cell
+    one = wl.cells.subset([5])
+    g = gpu_run(kt, wl.network, one, 10.0, opts, net)
+    o = ora_run(oracle_mod, wl.network, one, 10.0, wl.tol)
+    assert compare(g, o, 0).ok()
+    # non-finite and negative inputs, and a cell that must revert
+    c = wl.cells
+    c.y[0, 1] = np.nan
+    c.T[2] = np.inf
+    c.y[2, 3] = -1e-3
+    g = gpu_run(kt, wl.network, c, 10.0, opts, net)
+    o = ora_run(oracle_mod, wl.network, c, 10.0, wl.tol)
+    assert list(g["status"][:4]) == [0, 3, 3, 0]
+    assert np.isnan(g["y"][0, 1])
+    rep = compare({k: np.delete(v, [1, 2], axis=-1) for k, v in g.items()},
+                  {k: np.delete(v, [1, 2], axis=-1) for k, v in o.items()}, 0)
+    assert rep.ok(), rep
+    g = gpu_run(kt, wl.network, wl.cells.subset(range(3, 40)), 1e4,
+                kt.options(wl.tol, max_substeps=50), net)
+    assert np.all(g["status"] == 2)
+    assert np.array_equal(g["y"], np.maximum(wl.cells.subset(range(3, 40)).y, 0))
+
+
+@pytest.mark.parametrize("form", [0, 1])
+def test_split_range_bit_identical_and_deterministic(kt, form):
+    wl = I.workload(2, 200)
+    net = kt.Network(wl.network)
+    opts = kt.options(wl.tol, form=form, persistent=1)
+    a = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, opts, net)
+    b = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, opts, net)
+    lo = gpu_run(kt, wl.network, wl.cells.subset(range(0, 77)), wl.tol.dt, opts, net)
+    hi = gpu_run(kt, wl.network, wl.cells.subset(range(77, 200)), wl.tol.dt, opts, net)
+    for k in ("y", "T", "status", "nsub", "nnewton"):
+        assert np.array_equal(a[k], b[k]), k
+        assert np.array_equal(a[k], np.concatenate([lo[k], hi[k]], axis=-1)), k
+    # persistent and one-pass launches compute the same cells bit for bit
+    c = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, kt.options(wl.tol, form=form, persistent=0), net)
+    for k in ("y", "T", "status", "nsub", "nnewton"):
+        assert np.array_equal(a[k], c[k]), k
+
+
+def test_state_api_host_roundtrip(kt):
+    wl = I.workload(1, 100)
+    net = kt.Network(wl.network)
+    opts = kt.options(wl.tol, persistent=1)
+    st = kt.State(net, 100)
+    st.upload(wl.cells.y, wl.cells.T, wl.cells.rho)
+    st.integrate(wl.tol.dt, opts)
+    h = st.download()
+    d = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, opts, net)
+    for k in ("y", "T", "status", "nsub", "nnewton"):
+        assert np.array_equal(h[k], d[k]), k
