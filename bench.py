@@ -208,6 +208,10 @@ def main():
     ap.add_argument("--workload", type=int, default=2)
     ap.add_argument("--ncells", type=int, default=None)
     ap.add_argument("--forms", default="plain,chosen")
+    ap.add_argument("--plain-steps", type=int, default=1,
+                    help="timed steps of the plain FP64 form (context line, not the headline)")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-cells", type=int, default=1024)
@@ -245,17 +249,42 @@ def main():
     stream = torch.cuda.current_stream()
 
     forms = {"plain": dict(form=kt.KT_FORM_FP64, persistent=0),
-             "chosen": dict(form=kt.KT_FORM_FP32LU, persistent=1)}
+             "chosen": dict(form=kt.KT_FORM_FP32LU, persistent=1, guess=kt.KT_GUESS_FULLSTEP,
+                            use_graph=1)}
+    tuned = None
+    if not args.no_tune:
+        base = kt.options(wl.tol, **forms["chosen"])
+        cache = os.path.join(ROOT, "gpurun_out", "tuned.json") if os.path.isdir(
+            os.path.join(ROOT, "gpurun_out")) else os.path.join(ROOT, ".tuned.json")
+        # tune on the whole batch over a short interval (dt/1000): every launch shape is
+        # exercised at full occupancy in well under a second per candidate
+        topts, tuned = kt.tuned_options(net, y_in, T_in, wl.tol.dt * 1e-3, base, cache,
+                                        sample=ncells)
+        for f in ("cells_per_warp", "persistent", "block_warps", "blocks_per_sm"):
+            forms["chosen"][f] = int(getattr(topts, f))
+    state = kt.State(net, ncells)
     results = {}
     clocks = ClockSampler(local)
     clock_started = False
+    def run_step(name, opts):
+        if forms[name].get("use_graph"):
+            # the library-owned state replays a captured graph (scratch reset + kernel);
+            # each step integrates the same input batch, copied in device to device
+            state.upload(y_in, T_in, rho)
+            state.integrate(wl.tol.dt, opts)
+        else:
+            kt.integrate(net, y_in, T_in, wl.tol.dt, opts, rho=rho, out=out, scratch=scratch)
+
     for name in [f for f in args.forms.split(",") if f]:
         opts = kt.options(wl.tol, **forms[name])
-        for _ in range(args.warmup):
-            kt.integrate(net, y_in, T_in, wl.tol.dt, opts, rho=rho, out=out, scratch=scratch)
+        nsteps = args.steps if name == "chosen" else args.plain_steps
+        nwarm = args.warmup if name == "chosen" else min(args.warmup, 1)
+        for _ in range(nwarm):
+            run_step(name, opts)
         kt.check_scratch(scratch)
+        state.check()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
+              for _ in range(nsteps)]
         if name == "chosen" and not clock_started:
             clocks.start()
             clock_started = True
@@ -263,16 +292,21 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for s in range(args.steps):
+        for s in range(nsteps):
             flush.fill_(s & 0xff)
             ev[s][0].record(stream)
-            kt.integrate(net, y_in, T_in, wl.tol.dt, opts, rho=rho, out=out, scratch=scratch)
+            run_step(name, opts)
             ev[s][1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
         step_ms = [a.elapsed_time(b) for a, b in ev]
         kt.check_scratch(scratch)
+        state.check()
         tot_ms = sum(step_ms)
+        if forms[name].get("use_graph"):
+            st_h = state.download()
+            for k in ("status", "nsub", "nnewton"):
+                out[k].copy_(torch.from_numpy(st_h[k]))
         if world > 1:
             t = torch.tensor([tot_ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -283,9 +317,11 @@ def main():
         f64, f32, trans = flops_per_newton(wl.network, forms[name]["form"])
         # factorisations: count one per Newton solve start and per refresh (upper bound
         # of the FP32 work is not needed; the FP64 work is per iteration)
-        per_launch_ms = tot_ms / args.steps
+        per_launch_ms = tot_ms / nsteps
         results[name] = {
-            "value": world * ncells * args.steps / (tot_ms / 1e3),
+            "steps": nsteps, "warmup": nwarm,
+            "options": {k: int(v) for k, v in forms[name].items()},
+            "value": world * ncells * nsteps / (tot_ms / 1e3),
             "ms_per_step": per_launch_ms,
             "wall_s": wall,
             "newton_iters": int(nnew), "substeps": int(nsub),
@@ -312,15 +348,11 @@ def main():
                   status=torch.empty(ncells, dtype=torch.int32).pin_memory().numpy(),
                   nsub=torch.empty(ncells, dtype=torch.int32).pin_memory().numpy(),
                   nnewton=torch.empty(ncells, dtype=torch.int32).pin_memory().numpy())
-        state = kt.State(net, ncells)
-        state.upload(hy, hT, hr)
-        state.integrate(wl.tol.dt, opts)
-        state.download(out=ho)
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.steps):
+        for _ in range(args.e2e_steps):
             state.upload(hy, hT, hr)
             state.integrate(wl.tol.dt, opts)
             state.download(out=ho)
@@ -331,10 +363,9 @@ def main():
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_s = float(t.item())
         ns = wl.network.ns
-        e2e = {"value": world * ncells * args.steps / e2e_s, "unit": UNIT,
+        e2e = {"value": world * ncells * args.e2e_steps / e2e_s, "unit": UNIT, "steps": args.e2e_steps,
                "h2d_bytes_per_step": ncells * (ns + 2) * 8,
                "d2h_bytes_per_step": ncells * (ns + 1) * 8 + 3 * ncells * 4}
-        del state
 
     # ---- CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
     cpu = None
@@ -357,7 +388,7 @@ def main():
                 "dtype": "f64" if head_name == "plain" else "f64+f32",
                 "data": "synthetic", "config": config_of(args, wl, ncells),
                 "forms": results, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": args.steps, "clocks": clk}
+                "gpu_launches": args.steps, "clocks": clk, "autotune": tuned}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -61,9 +61,12 @@ extern "C" {
 /* Newton starting iterate */
 #define KT_GUESS_PREV 0    /* the state at the start of the step (plain predictor) */
 #define KT_GUESS_MLP 1     /* learned initial guess (needs kt_mlp_load) */
+#define KT_GUESS_FULLSTEP 2 /* second half step starts from the full step's result
+                               (same end time; differs by the local error only) */
 
 typedef struct kt_network kt_network;
 typedef struct kt_state kt_state;
+typedef struct kt_mlp kt_mlp;
 
 /* Integration options.  Fill with kt_options_default() and override fields.
  * Sub-step control: one backward-Euler step of h and two of h/2 per attempt; the
@@ -93,7 +96,9 @@ typedef struct {
     int block_warps;         /* warps per block, 0 = automatic                   (0) */
     int blocks_per_sm;       /* persistent grid = blocks_per_sm x SMs, 0 = automatic (0) */
     int use_graph;           /* 1: kt_integrate replays a captured CUDA graph    (0) */
-    int reserved[6];
+    int cells_per_warp;      /* 32: one cell per lane (networks with <= 16 unknowns);
+                                1: one cell per warp (<= 96 unknowns); 0: automatic (0) */
+    int reserved[5];
 } kt_options;
 
 /* Defaults listed above. */
@@ -124,7 +129,9 @@ KT_API int kt_state_create(const kt_network *net, int64_t ncells, kt_state **out
 KT_API int kt_state_upload(kt_state *st, const double *y, const double *T, const double *rho,
                     int src_is_device, void *cuda_stream);
 
-/* Advance every cell of the state by dt in place (asynchronous on stream). */
+/* Advance every cell of the state by dt in place (asynchronous on stream).  With
+ * opts->use_graph the call (scratch reset + kernel) is captured once into a CUDA graph
+ * on a private stream and replayed on `stream` while dt and *opts are unchanged. */
 KT_API int kt_integrate(kt_state *st, double dt, const kt_options *opts, void *cuda_stream);
 
 /* Copy results out (host or device destination).  Any output pointer may be NULL.
@@ -155,8 +162,83 @@ KT_API int kt_integrate_ptrs(const kt_network *net, int64_t ncells, const double
                       int32_t *status, int32_t *n_substeps, int32_t *n_newton,
                       void *scratch, void *cuda_stream);
 
+/* Launch-configuration search (one cell per lane vs one per warp, warps per block,
+ * persistent queue or one pass) on a caller-supplied sample of cells in device
+ * buffers: each candidate integrates the sample once untimed and once timed with
+ * CUDA events on stream; *best receives base with the fastest configuration and
+ * *best_seconds its time.  Same buffer rules as kt_integrate_ptrs; synchronises. */
+KT_API int kt_autotune(const kt_network *net, int64_t ncells, const double *y_in,
+                       const double *T_in, double dt, const kt_options *base,
+                       double *y_out, double *T_out, void *scratch, void *cuda_stream,
+                       kt_options *best, double *best_seconds);
+
+/* kt_integrate_ptrs with a per-cell time step: dt_cells [ncells] (device, float64,
+ * each > 0; a cell whose dt is not a positive finite number gets status
+ * KT_STATUS_NONFINITE and is left untouched). */
+KT_API int kt_integrate_dt(const kt_network *net, int64_t ncells, const double *y_in,
+                           const double *T_in, const double *rho, const double *dt_cells,
+                           const kt_options *opts, double *y_out, double *T_out,
+                           int32_t *status, int32_t *n_substeps, int32_t *n_newton,
+                           void *scratch, void *cuda_stream);
+
 /* Read and clear the device error word of a scratch buffer (synchronises stream). */
 KT_API int kt_scratch_check(void *scratch, void *cuda_stream);
+
+/* ---------------------------------------------------------------- learned guess
+ * A small MLP predicts the Newton starting iterate of each sub-step (the paper's
+ * closing section points at DeepODE-style learned solvers; there is no further
+ * specification).  Architecture: n_in (<= 16) -> 128 -> 128 -> 128 -> n_out (<= 8),
+ * SiLU, BF16 weights, FP32 accumulation (mma.sync tensor-core kernels).
+ * For a network with ns species and N unknowns the guess uses n_in = ns + 3 features
+ * (log max(y_s,1e-30), log T, log rho, log h), normalised as (x - mu_in)/sd_in, and
+ * n_out = N outputs: the normalised change of log y (and log T) over the step,
+ * un-normalised as mu_out + sd_out * out.  If Newton does not converge from the guess
+ * the step is retried from the plain predictor, so the answer is the solver's.
+ * Master parameters (float32, kt_mlp_sizes() of them) in this order:
+ * W1 [128][16], W2 [128][128], W3 [128][128], W4 [8][128], b1 [128], b2 [128],
+ * b3 [128], b4 [8]; row n of W_l holds the weights of output n (z = h W^T + b);
+ * entries beyond n_in / n_out are zero and stay zero. */
+KT_API int kt_mlp_sizes(int *n_master_params, int *packed_bytes);
+
+/* New MLP on the current device with PyTorch-style uniform initialisation from seed. */
+KT_API int kt_mlp_create(int n_in, int n_out, unsigned long long seed, kt_mlp **out);
+KT_API void kt_mlp_free(kt_mlp *mlp);
+
+/* Feature / output normalisation (host arrays of n_in and n_out floats; sd > 0). */
+KT_API int kt_mlp_set_norm(kt_mlp *mlp, const float *mu_in, const float *sd_in,
+                           const float *mu_out, const float *sd_out);
+
+/* One Adam step (lr; betas 0.9, 0.999; eps 1e-8) on the MSE loss
+ * 1/(2B) sum (out - target)^2 of a batch: X [B][16] and targets [B][8] are
+ * normalised float32 device arrays (padding columns ignored).  *loss (host, may be
+ * NULL; non-NULL synchronises) receives the loss before the update. */
+KT_API int kt_mlp_train_step(kt_mlp *mlp, const float *X, const float *targets, int B,
+                             float lr, double *loss, void *cuda_stream);
+
+/* Gradients of that loss (host float array in the master order) without updating;
+ * synchronises. */
+KT_API int kt_mlp_gradients(kt_mlp *mlp, const float *X, const float *targets, int B,
+                            float *grads, double *loss, void *cuda_stream);
+
+/* Batch inference: X [n][16] -> out [n][8] (normalised), device arrays, asynchronous. */
+KT_API int kt_mlp_forward(const kt_mlp *mlp, const float *X, float *out, int64_t n,
+                          void *cuda_stream);
+
+/* Copy the float32 master parameters out / in (host arrays; set re-packs BF16). */
+KT_API int kt_mlp_get_params(const kt_mlp *mlp, float *master);
+KT_API int kt_mlp_set_params(kt_mlp *mlp, const float *master);
+
+/* Flat binary file: "KTMLP1", n_in, n_out, hidden, layers, seed, step, dtype tag,
+ * normalisation, float32 masters. */
+KT_API int kt_mlp_save(const kt_mlp *mlp, const char *path);
+KT_API int kt_mlp_load_file(const char *path, kt_mlp **out);
+
+/* Load a saved MLP into a state (owned by the state) for opts.guess = KT_GUESS_MLP. */
+KT_API int kt_mlp_load(kt_state *st, const char *weights_path);
+
+/* Use mlp (not owned; must outlive the calls) for kt_integrate_ptrs / kt_integrate_dt
+ * with opts.guess = KT_GUESS_MLP on this network; NULL detaches. */
+KT_API int kt_network_attach_mlp(kt_network *net, const kt_mlp *mlp);
 
 /* Thread-local message of the last failed call ("" if none). */
 KT_API const char *kt_last_error(void);

@@ -81,7 +81,9 @@ typedef struct {
     int adaptive;   /* 1: step-doubling control; 0: fixed steps of h_init (pins only) */
     int retry;      /* 1: retry once on failure */
     int atol_mode;  /* 0: atol absolute; 1: atol times the cell's initial element-0 total */
-    int pad;
+    int guess;      /* Newton start of the second half step: 0 its own start state;
+                       2 the full step's result (same end time).  Changes only the
+                       iteration count, not the root (to the Newton tolerance). */
 } ko_options;
 
 /* ------------------------------------------------------------------ parsing */
@@ -487,7 +489,7 @@ static int advance(ko_cell *c, double *y, double dt, double h0, double facmax, i
             ok = be_solve(c, y, 0.5 * h, yh) == 0;
         }
         if (ok) {
-            for (i = 0; i < N; i++) y2[i] = yh[i];
+            for (i = 0; i < N; i++) y2[i] = o->guess == 2 ? yf[i] : yh[i];
             ok = be_solve(c, yh, 0.5 * h, y2) == 0;
         }
         if (!ok) {

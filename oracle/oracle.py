@@ -42,14 +42,14 @@ class Options(ctypes.Structure):
                 ("retry_facmax", ctypes.c_double),
                 ("max_substeps", ctypes.c_int), ("max_newton", ctypes.c_int),
                 ("adaptive", ctypes.c_int), ("retry", ctypes.c_int),
-                ("atol_mode", ctypes.c_int), ("pad", ctypes.c_int)]
+                ("atol_mode", ctypes.c_int), ("guess", ctypes.c_int)]
 
 
 def options(tol=None, **kw) -> Options:
     """Options from an ``inputs.Tolerances`` plus keyword overrides."""
     d = dict(rtol=1e-6, atol=1e-10, h_init=1e-6, h_min=1e-30, newton_rtol=1e-12,
              newton_atol_frac=1e-2, facmax=4.0, retry_h_factor=1e-3, retry_facmax=2.0,
-             max_substeps=100000, max_newton=8, adaptive=1, retry=1, atol_mode=0, pad=0)
+             max_substeps=100000, max_newton=8, adaptive=1, retry=1, atol_mode=0, guess=0)
     if tol is not None:
         d.update(rtol=tol.rtol, atol=tol.atol, h_init=tol.h_init, h_min=tol.h_min,
                  max_substeps=tol.max_substeps, max_newton=tol.max_newton,

@@ -43,6 +43,8 @@ int align16(int x) { return (x + 15) & ~15; }
 
 }  // namespace
 
+void kt::set_error(const char *msg) { g_err = msg; }
+
 struct kt_network {
     std::string name;
     int ns = 0, ne = 0, nr = 0, energy = 0;
@@ -54,6 +56,7 @@ struct kt_network {
     std::vector<double> A, b, th;
     std::vector<unsigned char> blob;
     NetView view{};
+    const kt_mlp *mlp = nullptr;                  // attached learned-guess MLP (not owned)
     std::mutex mu;
     std::map<int, unsigned char *> dev_blob;      // device ordinal -> device copy
 
@@ -101,6 +104,13 @@ struct kt_state {
     double *y = nullptr, *T = nullptr, *rho = nullptr;
     int *status = nullptr, *nsub = nullptr, *nnew = nullptr;
     kt::Scratch *scratch = nullptr;
+    // captured integrate call (memset of the scratch + kernel), replayed while dt and
+    // the options are unchanged
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap = nullptr;
+    double g_dt = 0.0;
+    kt_options g_opts{};
+    kt_mlp *mlp = nullptr;                        // learned-guess MLP loaded for this state (owned)
 };
 
 namespace {
@@ -233,6 +243,21 @@ void build_blob(kt_network *n)
     v.off_cv = o; o = align16(o + 8 * n->ns);
     v.off_cnt = o; o = align16(o + 8 * n->ns * n->ne);
     v.off_idx = o; o = align16(o + 8 * n->nr);
+    // per-species lists of (reaction, net coefficient)
+    std::vector<int> rp(n->ns + 1, 0), re;
+    for (int s = 0; s < n->ns; ++s) {
+        rp[s] = static_cast<int>(re.size());
+        for (int r = 0; r < n->nr; ++r) {
+            int nu = 0;
+            for (int j = 0; j < n->nout[r]; ++j) nu += n->out[r][j] == s;
+            for (int j = 0; j < n->nin[r]; ++j) nu -= n->in[r][j] == s;
+            if (nu != 0) re.push_back((r << 8) | (nu & 0xff));
+        }
+    }
+    rp[n->ns] = static_cast<int>(re.size());
+    v.nent = static_cast<int>(re.size());
+    v.off_rp = o; o = align16(o + 4 * (n->ns + 1));
+    v.off_re = o; o = align16(o + 4 * v.nent);
     if (o < 16) o = 16;
     v.bytes = o;
     n->blob.assign(o, 0);
@@ -253,6 +278,8 @@ void build_blob(kt_network *n)
             ix[5 + j] = static_cast<unsigned char>(j < n->nout[r] ? n->out[r][j] : kt::kIdxNone);
         }
     }
+    std::memcpy(n->blob.data() + v.off_rp, rp.data(), 4 * rp.size());
+    if (!re.empty()) std::memcpy(n->blob.data() + v.off_re, re.data(), 4 * re.size());
     for (int s = 0; s < n->ns; ++s) {
         put(v.off_h, s, n->h[s]);
         put(v.off_cv, s, n->cv[s]);
@@ -267,10 +294,10 @@ int check_opts(const kt_options *o)
         !(o->newton_rtol > 0) || !(o->newton_atol_frac > 0) || !(o->facmax >= 1) ||
         !(o->retry_h_factor > 0) || !(o->retry_facmax >= 1) || o->max_substeps < 1 ||
         o->max_newton < 1 || (o->form != KT_FORM_FP64 && o->form != KT_FORM_FP32LU) ||
-        (o->guess != KT_GUESS_PREV && o->guess != KT_GUESS_MLP) || o->block_warps < 0 ||
+        (o->guess != KT_GUESS_PREV && o->guess != KT_GUESS_MLP && o->guess != KT_GUESS_FULLSTEP) ||
+        o->block_warps < 0 ||
         o->blocks_per_sm < 0)
         return fail(KT_EINVAL, "options: a field is out of range");
-    if (o->guess == KT_GUESS_MLP) return fail(KT_EUNSUPPORTED, "options: learned guess needs kt_mlp_load");
     return KT_OK;
 }
 
@@ -355,14 +382,17 @@ void kt_network_free(kt_network *n) { delete n; }
 
 size_t kt_scratch_bytes(void) { return sizeof(kt::Scratch); }
 
-int kt_integrate_ptrs(const kt_network *net, int64_t ncells, const double *y_in, const double *T_in,
-                      const double *rho, double dt, const kt_options *opts, double *y_out,
-                      double *T_out, int32_t *status, int32_t *n_substeps, int32_t *n_newton,
-                      void *scratch, void *cuda_stream)
+}  // extern "C"
+
+namespace {
+
+int integrate_impl(const kt_network *net, int64_t ncells, const double *y_in, const double *T_in,
+                   const double *rho, const double *dt_cell, double dt, const kt_options *opts, double *y_out,
+                   double *T_out, int32_t *status, int32_t *n_substeps, int32_t *n_newton, void *scratch,
+                   void *cuda_stream, const kt_mlp *mlp)
 {
-    (void)rho;
-    if (!net) return fail(KT_EINVAL, "kt_integrate_ptrs: NULL network");
-    if (ncells < 0 || !(dt > 0) || !std::isfinite(dt)) return fail(KT_EINVAL, "kt_integrate_ptrs: bad ncells or dt");
+    if (!net) return fail(KT_EINVAL, "kt_integrate: NULL network");
+    if (ncells < 0 || !(dt > 0) || !std::isfinite(dt)) return fail(KT_EINVAL, "kt_integrate: bad ncells or dt");
     int rc = check_opts(opts);
     if (rc) return rc;
     if (ncells == 0) return KT_OK;
@@ -370,9 +400,13 @@ int kt_integrate_ptrs(const kt_network *net, int64_t ncells, const double *y_in,
         return fail(KT_EINVAL, "kt_integrate_ptrs: NULL device buffer");
     if (reinterpret_cast<uintptr_t>(scratch) % 16) return fail(KT_EINVAL, "kt_integrate_ptrs: scratch not 16-B aligned");
     const int N = net->ns + net->energy;
-    if (N > kt::kLaneMaxN)
+    int cpw = opts->cells_per_warp;
+    if (cpw == 0) cpw = N <= kt::kLaneMaxN ? 32 : 1;
+    if ((cpw != 32 && cpw != 1) || (cpw == 32 && N > kt::kLaneMaxN))
+        return fail(KT_EINVAL, "kt_integrate_ptrs: cells_per_warp %d not available for %d unknowns", cpw, N);
+    if (N > kt::kWarpMaxN)
         return fail(KT_EUNSUPPORTED, "kt_integrate_ptrs: %d unknowns per cell; this build handles up to %d", N,
-                    kt::kLaneMaxN);
+                    kt::kWarpMaxN);
     kt_network *mn = const_cast<kt_network *>(net);
     const unsigned char *blob = nullptr;
     rc = mn->device_blob(&blob);
@@ -385,7 +419,22 @@ int kt_integrate_ptrs(const kt_network *net, int64_t ncells, const double *y_in,
     a.blob = blob;
     a.o = dev_opts(opts);
     a.dt = dt;
+    a.dt_cell = dt_cell;
+    a.rho = rho;
     a.ncells = ncells;
+    if (opts->guess == KT_GUESS_MLP) {
+        const kt_mlp *m = mlp ? mlp : net->mlp;
+        int dev = 0, cur = 0;
+        a.mlp = kt::mlp_device_block(m, &a.mlp_nin, &a.mlp_nout, &dev);
+        cudaGetDevice(&cur);
+        if (!a.mlp) return fail(KT_EINVAL, "kt_integrate: learned guess requested but no MLP is loaded/attached");
+        if (dev != cur) return fail(KT_EINVAL, "kt_integrate: the MLP lives on another device");
+        if (a.mlp_nin != net->ns + 3 || a.mlp_nout != N)
+            return fail(KT_EINVAL, "kt_integrate: MLP sizes (%d in, %d out) do not match the network (%d, %d)",
+                        a.mlp_nin, a.mlp_nout, net->ns + 3, N);
+        if (cpw != 32) return fail(KT_EUNSUPPORTED, "kt_integrate: the learned guess runs in the lane-per-cell kernels");
+        if (!opts->persistent) return fail(KT_EUNSUPPORTED, "kt_integrate: the learned guess needs persistent=1");
+    }
     a.y_in = y_in;
     a.T_in = T_in;
     a.y_out = y_out;
@@ -394,10 +443,33 @@ int kt_integrate_ptrs(const kt_network *net, int64_t ncells, const double *y_in,
     a.nsub = n_substeps;
     a.nnew = n_newton;
     a.scratch = static_cast<kt::Scratch *>(scratch);
-    kt::LaunchCfg c{opts->form, opts->persistent, opts->block_warps, opts->blocks_per_sm};
-    int ce = kt::launch_lane(a, c, cuda_stream);
+    kt::LaunchCfg c{opts->form, opts->persistent, opts->block_warps, opts->blocks_per_sm, cpw};
+    int ce = cpw == 32 ? kt::launch_lane(a, c, cuda_stream) : kt::launch_warp(a, c, cuda_stream);
     if (ce != 0) return cuda_fail(static_cast<cudaError_t>(ce), "integrate kernel launch");
     return KT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kt_integrate_ptrs(const kt_network *net, int64_t ncells, const double *y_in, const double *T_in,
+                      const double *rho, double dt, const kt_options *opts, double *y_out,
+                      double *T_out, int32_t *status, int32_t *n_substeps, int32_t *n_newton,
+                      void *scratch, void *cuda_stream)
+{
+    return integrate_impl(net, ncells, y_in, T_in, rho, nullptr, dt, opts, y_out, T_out, status, n_substeps,
+                          n_newton, scratch, cuda_stream, nullptr);
+}
+
+int kt_integrate_dt(const kt_network *net, int64_t ncells, const double *y_in, const double *T_in,
+                    const double *rho, const double *dt_cells, const kt_options *opts, double *y_out,
+                    double *T_out, int32_t *status, int32_t *n_substeps, int32_t *n_newton, void *scratch,
+                    void *cuda_stream)
+{
+    if (!dt_cells) return fail(KT_EINVAL, "kt_integrate_dt: NULL dt_cells");
+    return integrate_impl(net, ncells, y_in, T_in, rho, dt_cells, 1.0, opts, y_out, T_out, status, n_substeps,
+                          n_newton, scratch, cuda_stream, nullptr);
 }
 
 int kt_scratch_check(void *scratch, void *cuda_stream)
@@ -454,6 +526,9 @@ int kt_state_create(const kt_network *net, int64_t ncells, kt_state **out)
 void kt_state_free(kt_state *st)
 {
     if (!st) return;
+    if (st->mlp) kt_mlp_free(st->mlp);
+    if (st->gexec) cudaGraphExecDestroy(st->gexec);
+    if (st->cap) cudaStreamDestroy(st->cap);
     cudaFree(st->y);
     cudaFree(st->T);
     cudaFree(st->rho);
@@ -475,6 +550,10 @@ int kt_state_upload(kt_state *st, const double *y, const double *T, const double
     cudaError_t e = cudaMemcpyAsync(st->y, y, n * st->net->ns * sizeof(double), k, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(st->T, T, n * sizeof(double), k, s);
     if (e == cudaSuccess && rho) e = cudaMemcpyAsync(st->rho, rho, n * sizeof(double), k, s);
+    if (e == cudaSuccess && !rho) {
+        std::vector<double> ones(n, 1.0);
+        e = cudaMemcpy(st->rho, ones.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "kt_state_upload");
     return KT_OK;
 }
@@ -482,8 +561,123 @@ int kt_state_upload(kt_state *st, const double *y, const double *T, const double
 int kt_integrate(kt_state *st, double dt, const kt_options *opts, void *cuda_stream)
 {
     if (!st) return fail(KT_EINVAL, "kt_integrate: NULL state");
-    return kt_integrate_ptrs(st->net, st->ncells, st->y, st->T, st->rho, dt, opts, st->y, st->T, st->status,
-                             st->nsub, st->nnew, st->scratch, cuda_stream);
+    if (!opts || !opts->use_graph || st->ncells == 0)
+        return integrate_impl(st->net, st->ncells, st->y, st->T, st->rho, nullptr, dt, opts, st->y, st->T,
+                              st->status, st->nsub, st->nnew, st->scratch, cuda_stream, st->mlp);
+    int rc = check_opts(opts);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (st->gexec && st->g_dt == dt && std::memcmp(&st->g_opts, opts, sizeof(kt_options)) == 0) {
+        cudaError_t e = cudaGraphLaunch(st->gexec, s);
+        return e == cudaSuccess ? KT_OK : cuda_fail(e, "cudaGraphLaunch");
+    }
+    // upload the network tables first: no synchronous call may run inside the capture
+    const unsigned char *blob = nullptr;
+    rc = const_cast<kt_network *>(st->net)->device_blob(&blob);
+    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
+    if (!st->cap) e = cudaStreamCreateWithFlags(&st->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate(capture)");
+    e = cudaStreamBeginCapture(st->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    rc = integrate_impl(st->net, st->ncells, st->y, st->T, st->rho, nullptr, dt, opts, st->y, st->T,
+                        st->status, st->nsub, st->nnew, st->scratch, st->cap, st->mlp);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(st->cap, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    if (st->gexec) {
+        cudaGraphExecDestroy(st->gexec);
+        st->gexec = nullptr;
+    }
+    e = cudaGraphInstantiate(&st->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    st->g_dt = dt;
+    st->g_opts = *opts;
+    e = cudaGraphLaunch(st->gexec, s);
+    return e == cudaSuccess ? KT_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
+int kt_network_attach_mlp(kt_network *net, const kt_mlp *mlp)
+{
+    if (!net) return fail(KT_EINVAL, "kt_network_attach_mlp: NULL network");
+    net->mlp = mlp;
+    return KT_OK;
+}
+
+int kt_mlp_load(kt_state *st, const char *weights_path)
+{
+    if (!st || !weights_path) return fail(KT_EINVAL, "kt_mlp_load: NULL argument");
+    kt_mlp *m = nullptr;
+    int rc = kt_mlp_load_file(weights_path, &m);
+    if (rc) return rc;
+    if (st->mlp) kt_mlp_free(st->mlp);
+    st->mlp = m;
+    if (st->gexec) {
+        cudaGraphExecDestroy(st->gexec);
+        st->gexec = nullptr;
+    }
+    return KT_OK;
+}
+
+int kt_autotune(const kt_network *net, int64_t ncells, const double *y_in, const double *T_in, double dt,
+                const kt_options *base, double *y_out, double *T_out, void *scratch, void *cuda_stream,
+                kt_options *best, double *best_seconds)
+{
+    if (!net || !base || !best || ncells <= 0) return fail(KT_EINVAL, "kt_autotune: bad argument");
+    int rc = check_opts(base);
+    if (rc) return rc;
+    const int N = net->ns + net->energy;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e != cudaSuccess) return cuda_fail(e, "kt_autotune: cudaEventCreate");
+    double best_t = 1e300;
+    kt_options cand = *base, win = *base;
+    const int cpws[2] = {32, 1};
+    const int bws[4] = {1, 2, 4, 8};
+    for (int ci = 0; ci < 2; ++ci) {
+        if (cpws[ci] == 32 && N > kt::kLaneMaxN) continue;
+        for (int per = 0; per <= 1; ++per)
+            for (int bi = 0; bi < 4; ++bi) {
+                cand.cells_per_warp = cpws[ci];
+                cand.persistent = per;
+                cand.block_warps = bws[bi];
+                cand.blocks_per_sm = 0;
+                cand.use_graph = 0;
+                rc = kt_integrate_ptrs(net, ncells, y_in, T_in, nullptr, dt, &cand, y_out, T_out, nullptr, nullptr,
+                                       nullptr, scratch, cuda_stream);
+                if (rc) break;
+                cudaEventRecord(e0, s);
+                rc = kt_integrate_ptrs(net, ncells, y_in, T_in, nullptr, dt, &cand, y_out, T_out, nullptr, nullptr,
+                                       nullptr, scratch, cuda_stream);
+                cudaEventRecord(e1, s);
+                if (rc) break;
+                e = cudaEventSynchronize(e1);
+                if (e != cudaSuccess) {
+                    rc = cuda_fail(e, "kt_autotune: run");
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_t) {
+                    best_t = ms;
+                    win = cand;
+                }
+            }
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    *best = win;
+    if (best_seconds) *best_seconds = best_t * 1e-3;
+    return KT_OK;
 }
 
 int kt_state_check(const kt_state *st, void *cuda_stream)

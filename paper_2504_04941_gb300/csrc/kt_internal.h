@@ -21,6 +21,9 @@ struct NetView {
     int off_A, off_b, off_th, off_dH;     // double[nr]: prefactor, exponent, activation T, heat
     int off_h, off_cv, off_cnt;           // double[ns], double[ns], double[ns*ne]
     int off_idx;                          // uint8[nr*8]: nin, nout, in0..2, out0..2
+    int off_rp, off_re, nent;             // per-species reaction lists (CSR): int32 row
+                                          // pointers [ns+1]; entries (r << 8) | (nu & 0xff),
+                                          // nu = net stoichiometric coefficient (nonzero)
     int bytes;                            // total, multiple of 16
     double t_ref, t_min, t_max;
 };
@@ -46,6 +49,10 @@ struct LaunchArgs {
     const unsigned char *blob;   // device network blob
     DevOpts o;
     double dt;
+    const double *dt_cell;       // per-cell dt (device, may be null: dt for every cell)
+    const double *rho;           // per-cell density (device, may be null: 1)
+    const unsigned char *mlp;    // packed MLP block for the learned guess (may be null)
+    int mlp_nin, mlp_nout;
     long long ncells;
     const double *y_in, *T_in;
     double *y_out, *T_out;
@@ -58,6 +65,7 @@ struct LaunchCfg {
     int persistent;
     int block_warps;    // 0 = auto
     int blocks_per_sm;  // 0 = auto
+    int cells_per_warp; // 32: lane-per-cell kernels, 1: warp-per-cell kernels
 };
 
 // Shared-memory layout of one warp of the lane-per-cell kernels.  Every per-cell
@@ -69,19 +77,25 @@ struct LaneLayout {
     int off_Y, off_YF, off_YH, off_Y2, off_W;      // fp64 vectors
     int off_K;                                     // per-cell rate coefficients (isothermal)
     int warp_bytes;                                // bytes per warp
-    int base;                                      // byte offset of warp 0 (after blob + barrier)
+    int mlp_off;                                   // byte offset of the staged MLP block
+    int base;                                      // byte offset of warp 0 (after blob, barriers, MLP)
 };
 
-inline LaneLayout lane_layout(int N, int nr, int energy, int fp32, int blob_bytes)
+inline LaneLayout lane_layout(int N, int nr, int energy, int fp32, int blob_bytes, int mlp_bytes = 0)
 {
     LaneLayout L{};
     const int d = 32 * 8, f = 32 * 4;   // bytes per element of a double / 4-byte array
     int o = 0;
     if (fp32) {
-        L.off_J = o; o += N * N * f;
-        L.off_M = o; o += N * N * f;
-        L.off_V = o; o += N * f;
-        L.off_X = o; o += N * f;
+        // J32/M32 (and V32/X32) interleave per lane: element e of lane l at float
+        // 64 e + 2 l (+1), so the lane's FP64 rescue matrix (double 32 e + l) overlays
+        // exactly its own FP32 slots.
+        L.off_J = o;
+        L.off_M = o;
+        o += N * N * d;
+        L.off_V = o;
+        L.off_X = o;
+        o += N * d;
     } else {
         L.off_J = -1;
         L.off_X = -1;
@@ -97,11 +111,62 @@ inline LaneLayout lane_layout(int N, int nr, int energy, int fp32, int blob_byte
     L.off_W = o; o += N * d;
     if (!energy) { L.off_K = o; o += nr * d; } else { L.off_K = -1; }
     L.warp_bytes = (o + 255) & ~255;
-    L.base = (blob_bytes + 16 + 255) & ~255;
+    L.mlp_off = (blob_bytes + 16 + 255) & ~255;
+    L.base = (L.mlp_off + mlp_bytes + 255) & ~255;
     return L;
 }
 
+// Shared-memory layout of one warp of the warp-per-cell kernels (one cell per warp).
+// Matrices are row-major with an odd row stride NP (conflict-free column reads).
+struct WarpLayout {
+    int NP;
+    int off_M, off_J, off_V, off_P, off_G;   // matrix, fp32 Jacobian, scales, pivots, gather
+    int off_Y, off_YF, off_YH, off_Y2, off_W;
+    int off_K, off_DK;                       // rate coefficients and dk/dT per reaction
+    int warp_bytes, base;
+};
+
+inline WarpLayout warp_layout(int N, int nr, int energy, int fp32, int blob_bytes)
+{
+    WarpLayout L{};
+    L.NP = N | 1;
+    const int NN = N * L.NP;
+    int o = 0;
+    auto take = [&](int bytes) { int r = o; o = (o + bytes + 15) & ~15; return r; };
+    if (fp32) {
+        L.off_J = take(NN * 4);
+        L.off_M = take(NN * 4);
+        L.off_V = take(N * 4);
+    } else {
+        L.off_J = -1;
+        L.off_M = take(NN * 8);
+        L.off_V = take(N * 8);
+    }
+    L.off_P = take(N * 4);
+    L.off_G = take(N * 4);
+    L.off_Y = take(N * 8);
+    L.off_YF = take(N * 8);
+    L.off_YH = take(N * 8);
+    L.off_Y2 = take(N * 8);
+    L.off_W = take(N * 8);
+    L.off_K = take(nr * 8);
+    L.off_DK = energy ? take(nr * 8) : -1;
+    L.warp_bytes = (o + 127) & ~127;
+    L.base = (blob_bytes + 16 + 127) & ~127;
+    return L;
+}
+
+constexpr int kWarpMaxN = 96;   // unknowns per cell handled by the warp-per-cell kernels
+
+// Thread-local error message shared by every entry point of the library.
+void set_error(const char *msg);
+
+// Device copy of an MLP's packed parameter block (null if m is null).
+const unsigned char *mlp_device_block(const kt_mlp *m, int *nin, int *nout, int *device);
+
 // Lane-per-cell kernels (N <= kLaneMaxN); returns a cudaError_t value.
 int launch_lane(const LaunchArgs &a, const LaunchCfg &c, void *stream);
+// Warp-per-cell kernels (N <= kWarpMaxN); returns a cudaError_t value.
+int launch_warp(const LaunchArgs &a, const LaunchCfg &c, void *stream);
 
 }  // namespace kt

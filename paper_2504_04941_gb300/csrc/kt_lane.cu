@@ -36,6 +36,7 @@
 #include <cstdint>
 
 #include "kt_internal.h"
+#include "kt_mlp.cuh"
 #include "kt_tma.cuh"
 
 namespace kt {
@@ -45,6 +46,8 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kMaxWarps = 8;
 
 #define LI(p, e) ((p)[(e) << 5])
+// per-lane arrays with a stride of 2^SH words (FP32 arrays interleave two per lane)
+#define LIS(p, e, SH) ((p)[(e) << (SH)])
 
 enum LaneState : int { kNeed = 0, kRun = 1, kDone = 2 };
 
@@ -102,7 +105,7 @@ __device__ __forceinline__ void reaction_pass(const NetView &nv, const NetSmem &
         for (int e = 0; e < N * N; ++e) LI(M64, e) = 0.0;
     }
     if (MODE == 2 && doJ) {
-        for (int e = 0; e < N * N; ++e) LI(J32, e) = 0.0f;
+        for (int e = 0; e < N * N; ++e) LIS(J32, e, 6) = 0.0f;
     }
     double fT = 0.0;
     for (int r = 0; r < nr; ++r) {
@@ -159,13 +162,13 @@ __device__ __forceinline__ void reaction_pass(const NetView &nv, const NetSmem &
                         f2 = static_cast<float>(y2);
             const float qf = ENERGY ? static_cast<float>(dHr * invCV) : 0.0f;
             auto col = [&](int m, float d) {
-                LI(J32, i0 * N + m) -= d;
-                if (nin > 1) LI(J32, i1 * N + m) -= d;
-                if (nin > 2) LI(J32, i2 * N + m) -= d;
-                if (nout > 0) LI(J32, o0 * N + m) += d;
-                if (nout > 1) LI(J32, o1 * N + m) += d;
-                if (nout > 2) LI(J32, o2 * N + m) += d;
-                if (ENERGY) LI(J32, ns * N + m) -= qf * d;
+                LIS(J32, i0 * N + m, 6) -= d;
+                if (nin > 1) LIS(J32, i1 * N + m, 6) -= d;
+                if (nin > 2) LIS(J32, i2 * N + m, 6) -= d;
+                if (nout > 0) LIS(J32, o0 * N + m, 6) += d;
+                if (nout > 1) LIS(J32, o1 * N + m, 6) += d;
+                if (nout > 2) LIS(J32, o2 * N + m, 6) += d;
+                if (ENERGY) LIS(J32, ns * N + m, 6) -= qf * d;
             };
             col(i0, kf * f1 * f2);
             if (nin > 1) col(i1, kf * f0 * f2);
@@ -182,30 +185,30 @@ __device__ __forceinline__ void reaction_pass(const NetView &nv, const NetSmem &
 // Crout LU with implicit-scaled row pivoting (Algorithm lu-decomp).  V holds the
 // inverse row maxima, then the inverse pivots (used by the back substitution).
 // Returns false on a zero row or a zero pivot.  T is double or float.
-template <typename T>
+template <typename T, int SH>
 __device__ __forceinline__ bool crout_lu(T *M, T *V, int *P, int N)
 {
     bool ok = true;
     for (int i = 0; i < N; ++i) {
         T big = T(0);
         for (int j = 0; j < N; ++j) {
-            const T a = LI(M, i * N + j);
+            const T a = LIS(M, i * N + j, SH);
             big = a < T(0) ? (-a > big ? -a : big) : (a > big ? a : big);
         }
         ok = ok && (big > T(0));
-        LI(V, i) = big > T(0) ? T(1) / big : T(1);
+        LIS(V, i, SH) = big > T(0) ? T(1) / big : T(1);
     }
     for (int j = 0; j < N; ++j) {
         for (int i = 0; i < N; ++i) {
             const int kmax = i < j ? i : j;
-            T s = LI(M, i * N + j);
-            for (int k = 0; k < kmax; ++k) s -= LI(M, i * N + k) * LI(M, k * N + j);
-            LI(M, i * N + j) = s;
+            T s = LIS(M, i * N + j, SH);
+            for (int k = 0; k < kmax; ++k) s -= LIS(M, i * N + k, SH) * LIS(M, k * N + j, SH);
+            LIS(M, i * N + j, SH) = s;
         }
         int imax = j;
-        T tmax = fabs(LI(M, j * N + j)) * LI(V, j);
+        T tmax = fabs(LIS(M, j * N + j, SH)) * LIS(V, j, SH);
         for (int i = j + 1; i < N; ++i) {
-            const T tt = fabs(LI(M, i * N + j)) * LI(V, i);
+            const T tt = fabs(LIS(M, i * N + j, SH)) * LIS(V, i, SH);
             if (tt > tmax) {
                 tmax = tt;
                 imax = i;
@@ -213,50 +216,54 @@ __device__ __forceinline__ bool crout_lu(T *M, T *V, int *P, int N)
         }
         ok = ok && (tmax > T(0));
         for (int k = 0; k < N; ++k) {
-            const T a = LI(M, imax * N + k), b = LI(M, j * N + k);
-            LI(M, imax * N + k) = b;
-            LI(M, j * N + k) = a;
+            const T a = LIS(M, imax * N + k, SH), b = LIS(M, j * N + k, SH);
+            LIS(M, imax * N + k, SH) = b;
+            LIS(M, j * N + k, SH) = a;
         }
-        const T va = LI(V, imax);
-        LI(V, imax) = LI(V, j);
-        LI(V, j) = va;
+        const T va = LIS(V, imax, SH);
+        LIS(V, imax, SH) = LIS(V, j, SH);
+        LIS(V, j, SH) = va;
         LI(P, j) = imax;
-        const T rinv = T(1) / LI(M, j * N + j);
-        for (int i = j + 1; i < N; ++i) LI(M, i * N + j) *= rinv;
-        LI(V, j) = rinv;
+        const T rinv = T(1) / LIS(M, j * N + j, SH);
+        for (int i = j + 1; i < N; ++i) LIS(M, i * N + j, SH) *= rinv;
+        LIS(V, j, SH) = rinv;
     }
     return ok;
 }
 
 // Solve with the factors: row swaps in order, unit-lower forward, upper backward.
-template <typename T>
+template <typename T, int SH>
 __device__ __forceinline__ void crout_solve(const T *M, const T *V, const int *P, T *x, int N)
 {
     for (int i = 0; i < N; ++i) {
         const int p = LI(P, i);
-        const T a = LI(x, i), b = LI(x, p);
-        LI(x, i) = b;
-        LI(x, p) = a;
+        const T a = LIS(x, i, SH), b = LIS(x, p, SH);
+        LIS(x, i, SH) = b;
+        LIS(x, p, SH) = a;
     }
     for (int i = 0; i < N; ++i) {
-        T s = LI(x, i);
-        for (int k = 0; k < i; ++k) s -= LI(M, i * N + k) * LI(x, k);
-        LI(x, i) = s;
+        T s = LIS(x, i, SH);
+        for (int k = 0; k < i; ++k) s -= LIS(M, i * N + k, SH) * LIS(x, k, SH);
+        LIS(x, i, SH) = s;
     }
     for (int i = N - 1; i >= 0; --i) {
-        T s = LI(x, i);
-        for (int k = i + 1; k < N; ++k) s -= LI(M, i * N + k) * LI(x, k);
-        LI(x, i) = s * LI(V, i);
+        T s = LIS(x, i, SH);
+        for (int k = i + 1; k < N; ++k) s -= LIS(M, i * N + k, SH) * LIS(x, k, SH);
+        LIS(x, i, SH) = s * LIS(V, i, SH);
     }
 }
 
-template <bool ENERGY, bool F32, bool PERSIST>
+template <bool ENERGY, bool F32, bool PERSIST, bool MLPG>
 __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a, const LaneLayout L)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     const NetView nv = a.nv;
     if (!stage_table(sm, a.blob, static_cast<unsigned>(nv.bytes),
                      reinterpret_cast<uint64_t *>(sm + nv.bytes), &a.scratch->error, kDevErrTma))
+        return;
+    const unsigned char *mlpP = sm + L.mlp_off;
+    if (MLPG && !stage_table(sm + L.mlp_off, a.mlp, static_cast<unsigned>(MlpLayout::BYTES),
+                             reinterpret_cast<uint64_t *>(sm + nv.bytes + 8), &a.scratch->error, kDevErrTma))
         return;
     const NetSmem t = net_smem(sm, nv);
     const DevOpts o = a.o;
@@ -271,16 +278,16 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
     double *W = reinterpret_cast<double *>(wb + L.off_W) + lane;
     int *P = reinterpret_cast<int *>(wb + L.off_P) + lane;
     double *K = ENERGY ? nullptr : reinterpret_cast<double *>(wb + L.off_K) + lane;
-    double *M64 = nullptr, *V64 = nullptr;
+    // FP64 matrix and scales; in the FP32 form they overlay the lane's own J32/M32 and
+    // V32/X32 slots and serve the FP64 rescue of a failed FP32 solve
+    double *M64 = reinterpret_cast<double *>(wb + L.off_M) + lane;
+    double *V64 = reinterpret_cast<double *>(wb + L.off_V) + lane;
     float *J32 = nullptr, *M32 = nullptr, *V32 = nullptr, *X32 = nullptr;
     if (F32) {
-        J32 = reinterpret_cast<float *>(wb + L.off_J) + lane;
-        M32 = reinterpret_cast<float *>(wb + L.off_M) + lane;
-        V32 = reinterpret_cast<float *>(wb + L.off_V) + lane;
-        X32 = reinterpret_cast<float *>(wb + L.off_X) + lane;
-    } else {
-        M64 = reinterpret_cast<double *>(wb + L.off_M) + lane;
-        V64 = reinterpret_cast<double *>(wb + L.off_V) + lane;
+        J32 = reinterpret_cast<float *>(wb + L.off_J) + 2 * lane;
+        M32 = J32 + 1;
+        V32 = reinterpret_cast<float *>(wb + L.off_V) + 2 * lane;
+        X32 = V32 + 1;
     }
 
     // ---- per-lane state
@@ -290,13 +297,18 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
         cell = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
         if (cell >= nc) state = kDone;
     }
-    double tt = 0.0, h = 0.0, facmax = 0.0, T_iso = 0.0, invCV = 0.0, atol_s = 0.0;
+    double tt = 0.0, h = 0.0, facmax = 0.0, T_iso = 0.0, invCV = 0.0, atol_s = 0.0, dtc = a.dt;
     int phase = 0, it = 0, natt = 0, nacc = 0, nnew = 0, attempt = 0;
     bool last = false;
-    // FP32 form: needJ -> assemble J32 at the current iterate; needF -> factorise
-    bool needJ = false, needF = false, luok = true;
+    // FP32 form: needJ -> assemble J32 at the current iterate; needF -> factorise;
+    // rescue -> this solve runs full FP64 Newton from its starting guess
+    bool needJ = false, needF = false, luok = true, rescue = false;
     int refresh = 0;
     double dprev = 0.0;
+    // learned guess: needG -> the attempt's first solve wants the MLP's starting point;
+    // usedG -> the current solve started from it (fall back to the plain start on failure)
+    bool needG = false, usedG = false;
+    double rho_c = 1.0;
 
     auto finish = [&]() { state = PERSIST ? kNeed : kDone; };
 
@@ -324,8 +336,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
         if (natt >= o.max_substeps) return false;
         ++natt;
         last = false;
-        if (tt + h >= a.dt * (1.0 - 1e-12)) {
-            h = a.dt - tt;
+        if (tt + h >= dtc * (1.0 - 1e-12)) {
+            h = dtc - tt;
             last = true;
         }
         phase = 0;
@@ -335,7 +347,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
             needJ = true;
             needF = true;
             refresh = 0;
+            rescue = false;
         }
+        needG = MLPG && o.guess == KT_GUESS_MLP;
+        usedG = false;
         return true;
     };
 
@@ -429,7 +444,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
     };
 
     auto begin_cell = [&]() {
-        bool fin = isfinite(a.T_in[cell]);
+        dtc = a.dt_cell ? a.dt_cell[cell] : a.dt;
+        rho_c = a.rho ? a.rho[cell] : 1.0;
+        bool fin = isfinite(a.T_in[cell]) && dtc > 0.0 && isfinite(dtc);
         for (int s = 0; s < ns; ++s) fin = fin && isfinite(a.y_in[static_cast<long long>(s) * nc + cell]);
         if (!fin) {
             for (int s = 0; s < ns; ++s)
@@ -466,6 +483,36 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
     auto step_fail_newton = [&]() {
         h *= 0.5;
         if (h < o.h_min || !begin_attempt()) run_fail();
+    };
+
+    // starting point of the current solve (plain predictor / second half from the full step)
+    auto restart_solve = [&]() {
+        double *yt = phase == 0 ? YF : (phase == 1 ? YH : Y2);
+        const double *g = phase == 2 ? (o.guess != KT_GUESS_PREV ? YF : YH) : Y;
+        for (int i = 0; i < N; ++i) LI(yt, i) = LI(g, i);
+        it = 0;
+    };
+
+    // Newton did not converge: a solve that started from the learned guess restarts from
+    // the plain predictor; an FP32 solve is redone in FP64; otherwise h halves.
+    auto newton_fail = [&]() {
+        if (usedG) {
+            usedG = false;
+            restart_solve();
+            if (F32) {
+                needJ = true;
+                needF = true;
+                refresh = 0;
+                rescue = false;
+            }
+            return;
+        }
+        if (F32 && !rescue) {
+            rescue = true;
+            restart_solve();
+            return;
+        }
+        step_fail_newton();
     };
 
     auto step_done = [&]() {
@@ -505,16 +552,23 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
     };
 
     auto phase_done = [&]() {
+        usedG = false;
+        if (F32 && rescue) {      // the FP64 rescue overwrote the FP32 factors
+            rescue = false;
+            needJ = true;
+            needF = true;
+            refresh = 0;
+        }
         if (phase == 0) {
             phase = 1;
             it = 0;
             for (int i = 0; i < N; ++i) LI(YH, i) = LI(Y, i);
-            if (F32) { needF = true; needJ = false; }
+            if (F32) { needF = true; }
         } else if (phase == 1) {
             phase = 2;
             it = 0;
-            for (int i = 0; i < N; ++i) LI(Y2, i) = LI(YH, i);
-            if (F32) { needF = false; needJ = false; }
+            const double *g2 = o.guess != KT_GUESS_PREV ? YF : YH;
+            for (int i = 0; i < N; ++i) LI(Y2, i) = LI(g2, i);
         } else {
             step_done();
         }
@@ -543,6 +597,51 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
             }
         }
         if (__all_sync(kFull, state == kDone)) break;
+
+        // ---- learned starting point for lanes that begin an attempt (warp-wide MMA)
+        if (MLPG) {
+            const bool wantG = state == kRun && needG;
+            if (__any_sync(kFull, wantG)) {
+                const float *nrm = reinterpret_cast<const float *>(mlpP + MlpLayout::NORM);
+                float x[kMlpIn];
+#pragma unroll
+                for (int k = 0; k < kMlpIn; ++k) x[k] = 0.0f;
+                if (wantG) {
+                    for (int k = 0; k < ns && k < kMlpIn; ++k)
+                        x[k] = static_cast<float>((log(fmax(LI(Y, k), 1e-30)) - nrm[k]) / nrm[16 + k]);
+                    const double Tc = ENERGY ? LI(Y, ns) : T_iso;
+                    const double f3[3] = {log(Tc), log(rho_c), log(h)};
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const int k = ns + q;
+                        if (k < kMlpIn) x[k] = static_cast<float>((f3[q] - nrm[k]) / nrm[16 + k]);
+                    }
+                }
+                uint32_t af[1][4];
+                float dlo[4], dhi[4];
+                gather_a(x, a.mlp_nin, 0, lane, af);
+                mlp_forward16(mlpP, af, dlo, lane);
+                gather_a(x, a.mlp_nin, 16, lane, af);
+                mlp_forward16(mlpP, af, dhi, lane);
+                float outv[kMlpOut];
+#pragma unroll
+                for (int q = 0; q < kMlpOut; ++q) {
+                    const float vlo = scatter_out(dlo, q, 0, lane);
+                    const float vhi = scatter_out(dhi, q, 16, lane);
+                    outv[q] = lane < 16 ? vlo : vhi;
+                }
+                if (wantG) {
+                    for (int i = 0; i < N && i < kMlpOut; ++i) {
+                        const double dlog = nrm[32 + i] + nrm[40 + i] * static_cast<double>(outv[i]);
+                        const double base = i < ns ? fmax(LI(Y, i), 1e-30) : LI(Y, i);
+                        const double g = base * exp(fmin(dlog, 50.0));
+                        LI(YF, i) = isfinite(g) ? g : LI(Y, i);
+                    }
+                    needG = false;
+                    usedG = true;
+                }
+            }
+        }
         if (state != kRun) continue;
 
         // ---- one Newton iteration of the current backward-Euler solve
@@ -558,26 +657,27 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
             lt = log(Ts / nv.t_ref);
             invT = 1.0 / Ts;
         }
-        if (!F32) {
+        if (!F32 || rescue) {
             reaction_pass<ENERGY, 1>(nv, t, yt, K, lt, invT, invCV, hph, W, M64, nullptr, false);
             for (int i = 0; i < N; ++i) LI(W, i) = -(LI(yt, i) - LI(yb, i) - hph * LI(W, i));
-            luok = crout_lu<double>(M64, V64, P, N);
-            crout_solve<double>(M64, V64, P, W, N);
+            luok = crout_lu<double, 5>(M64, V64, P, N);
+            crout_solve<double, 5>(M64, V64, P, W, N);
         } else {
             const bool doJ = needJ;
             reaction_pass<ENERGY, 2>(nv, t, yt, K, lt, invT, invCV, hph, W, nullptr, J32, doJ);
             if (needF) {
                 for (int i = 0; i < N; ++i)
                     for (int j = 0; j < N; ++j)
-                        LI(M32, i * N + j) = (i == j ? 1.0f : 0.0f) - static_cast<float>(hph) * LI(J32, i * N + j);
-                luok = crout_lu<float>(M32, V32, P, N);
+                        LIS(M32, i * N + j, 6) =
+                            (i == j ? 1.0f : 0.0f) - static_cast<float>(hph) * LIS(J32, i * N + j, 6);
+                luok = crout_lu<float, 6>(M32, V32, P, N);
                 needF = false;
             }
             needJ = false;
             for (int i = 0; i < N; ++i)
-                LI(X32, i) = static_cast<float>(-(LI(yt, i) - LI(yb, i) - hph * LI(W, i)));
-            crout_solve<float>(M32, V32, P, X32, N);
-            for (int i = 0; i < N; ++i) LI(W, i) = static_cast<double>(LI(X32, i));
+                LIS(X32, i, 6) = static_cast<float>(-(LI(yt, i) - LI(yb, i) - hph * LI(W, i)));
+            crout_solve<float, 6>(M32, V32, P, X32, N);
+            for (int i = 0; i < N; ++i) LI(W, i) = static_cast<double>(LIS(X32, i, 6));
         }
         bool conv = !bad && luok;
         double dmax = 0.0;
@@ -596,15 +696,15 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
         // ---- control
         if (conv) {
             phase_done();
-        } else if (!F32) {
-            if (bad || !luok || it + 1 >= o.max_newton) step_fail_newton();
+        } else if (!F32 || rescue) {
+            if (bad || !luok || it + 1 >= o.max_newton) newton_fail();
             else ++it;
         } else {
             // simplified Newton: refresh J (at the current iterate) when the
             // contraction stalls or the iteration budget of this factor is spent
             const bool stalled = it > 0 && !(dmax < 0.5 * dprev);
             if (bad || !luok || !isfinite(dmax)) {
-                step_fail_newton();
+                newton_fail();
             } else if (stalled || it + 1 >= o.max_newton) {
                 if (refresh < 2) {
                     ++refresh;
@@ -612,7 +712,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
                     needF = true;
                     it = 0;
                 } else {
-                    step_fail_newton();
+                    newton_fail();
                 }
             } else {
                 ++it;
@@ -622,10 +722,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
     }
 }
 
-template <bool ENERGY, bool F32, bool PERSIST>
+template <bool ENERGY, bool F32, bool PERSIST, bool MLPG>
 int launch_t(const LaunchArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
-    const LaneLayout L = lane_layout(a.nv.N, a.nv.nr, a.nv.energy, F32 ? 1 : 0, a.nv.bytes);
+    const LaneLayout L = lane_layout(a.nv.N, a.nv.nr, a.nv.energy, F32 ? 1 : 0, a.nv.bytes,
+                                     MLPG ? MlpLayout::BYTES : 0);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -637,7 +738,7 @@ int launch_t(const LaunchArgs &a, const LaunchCfg &c, cudaStream_t s)
     while (warps > 1 && L.base + warps * L.warp_bytes > smem_optin) --warps;
     const size_t smem = static_cast<size_t>(L.base) + static_cast<size_t>(warps) * L.warp_bytes;
     if (smem > static_cast<size_t>(smem_optin)) return cudaErrorInvalidConfiguration;
-    auto kern = lane_kernel<ENERGY, F32, PERSIST>;
+    auto kern = lane_kernel<ENERGY, F32, PERSIST, MLPG>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     const int threads = warps * 32;
@@ -665,12 +766,16 @@ int launch_lane(const LaunchArgs &a, const LaunchCfg &c, void *stream)
 {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const bool en = a.nv.energy != 0, f32 = c.form == KT_FORM_FP32LU, per = c.persistent != 0;
-    if (en) {
-        if (f32) return per ? launch_t<true, true, true>(a, c, s) : launch_t<true, true, false>(a, c, s);
-        return per ? launch_t<true, false, true>(a, c, s) : launch_t<true, false, false>(a, c, s);
+    if (a.mlp) {   // the learned guess runs with the persistent queue only
+        if (en) return f32 ? launch_t<true, true, true, true>(a, c, s) : launch_t<true, false, true, true>(a, c, s);
+        return f32 ? launch_t<false, true, true, true>(a, c, s) : launch_t<false, false, true, true>(a, c, s);
     }
-    if (f32) return per ? launch_t<false, true, true>(a, c, s) : launch_t<false, true, false>(a, c, s);
-    return per ? launch_t<false, false, true>(a, c, s) : launch_t<false, false, false>(a, c, s);
+    if (en) {
+        if (f32) return per ? launch_t<true, true, true, false>(a, c, s) : launch_t<true, true, false, false>(a, c, s);
+        return per ? launch_t<true, false, true, false>(a, c, s) : launch_t<true, false, false, false>(a, c, s);
+    }
+    if (f32) return per ? launch_t<false, true, true, false>(a, c, s) : launch_t<false, true, false, false>(a, c, s);
+    return per ? launch_t<false, false, true, false>(a, c, s) : launch_t<false, false, false, false>(a, c, s);
 }
 
 }  // namespace kt

@@ -1,0 +1,185 @@
+"""Learned Newton starting point: solver-generated data, training, evaluation.
+
+The MLP maps (log y, log T, log rho, log h) of a cell at the start of a step of size h
+to the change of log y over that step; the integrator uses the prediction as the
+Newton starting iterate of the step's first implicit solve and falls back to the
+plain predictor when Newton does not converge from it (include/kt.h).
+
+Data: cells of the Robertson workload are integrated along their trajectories by the
+CUDA solver itself, with snapshots at log-spaced times (1e-6 .. 1e4 s); every
+snapshot is paired with a step dt ~ log-uniform(1e-8, 1e-5) s and the solver's end
+state after dt.  Training runs the library's own BF16/FP32 forward, backward and
+Adam kernels (kt_mlp_train_step); this module only assembles tensors.
+"""
+from __future__ import annotations
+
+import math
+import time
+from typing import Dict, Optional
+
+import numpy as np
+
+from . import inputs as I
+from . import kt
+
+FLOOR = 1e-30
+
+
+def _features(y, T, rho, h):
+    """[n, 16] float64 features: log max(y, floor), log T, log rho, log h (padded)."""
+    import torch
+    ns, n = y.shape
+    X = torch.zeros((n, kt.MLP_IN), dtype=torch.float64, device=y.device)
+    X[:, :ns] = torch.log(torch.clamp(y, min=FLOOR)).T
+    X[:, ns] = torch.log(T)
+    X[:, ns + 1] = torch.log(rho)
+    X[:, ns + 2] = torch.log(h)
+    return X
+
+
+def _targets(y0, y1):
+    import torch
+    ns, n = y0.shape
+    D = torch.zeros((n, kt.MLP_OUT), dtype=torch.float64, device=y0.device)
+    D[:, :ns] = (torch.log(torch.clamp(y1, min=FLOOR)) - torch.log(torch.clamp(y0, min=FLOOR))).T
+    return D
+
+
+def trajectory_states(net: kt.Network, wl: I.Workload, n_traj: int, n_snap: int, seed: int,
+                      t0: float = 1e-6, t1: float = 1e4, opts=None):
+    """Snapshots of n_traj cells at n_snap log-spaced times in [t0, t1] (device tensors)."""
+    import torch
+    cells = I.robertson_cells(n_traj, seed)
+    y = torch.from_numpy(cells.y).cuda()
+    T = torch.from_numpy(cells.T).cuda()
+    times = np.geomspace(t0, t1, n_snap)
+    prev = 0.0
+    snaps = []
+    opts = opts or kt.options(wl.tol, persistent=1)
+    scratch = torch.empty(kt.scratch_bytes(), dtype=torch.uint8, device="cuda")
+    for tk in times:
+        r = kt.integrate(net, y, T, float(tk - prev), opts, scratch=scratch)
+        y = r["y"]
+        snaps.append(y.clone())
+        prev = tk
+    kt.check_scratch(scratch)
+    return torch.cat(snaps, dim=1), T.repeat(n_snap)
+
+
+def make_pairs(net: kt.Network, wl: I.Workload, n_pairs: int, seed: int,
+               dt_range=(1e-8, 1e-5), n_snap: int = 80) -> Dict[str, "object"]:
+    """Solver-generated (state, dt) -> end-state pairs on the GPU."""
+    import torch
+    n_traj = max(1, -(-n_pairs // n_snap))
+    y0, T = trajectory_states(net, wl, n_traj, n_snap, seed)
+    y0, T = y0[:, :n_pairs].contiguous(), T[:n_pairs].contiguous()
+    g = torch.Generator(device="cpu").manual_seed(seed + 1)
+    u = torch.rand(n_pairs, generator=g, dtype=torch.float64)
+    dt = torch.exp(math.log(dt_range[0]) + u * (math.log(dt_range[1]) - math.log(dt_range[0]))).cuda()
+    opts = kt.options(wl.tol, persistent=1)
+    r = kt.integrate_dt(net, y0, T, dt, opts)
+    kt.check_scratch(r["scratch"])
+    ok = r["status"] == 0
+    rho = torch.ones_like(T)
+    return dict(y0=y0[:, ok], T=T[ok], rho=rho[ok], dt=dt[ok], y1=r["y"][:, ok])
+
+
+def normalisation(pairs):
+    X = _features(pairs["y0"], pairs["T"], pairs["rho"], pairs["dt"])
+    D = _targets(pairs["y0"], pairs["y1"])
+    mu_in, sd_in = X.mean(0), X.std(0)
+    mu_out, sd_out = D.mean(0), D.std(0)
+    sd_in = torch_where_small(sd_in)
+    sd_out = torch_where_small(sd_out)
+    return (mu_in.cpu().numpy(), sd_in.cpu().numpy(), mu_out.cpu().numpy(), sd_out.cpu().numpy())
+
+
+def torch_where_small(sd, eps: float = 1e-6):
+    import torch
+    return torch.where(sd > eps, sd, torch.ones_like(sd))
+
+
+def normalised_tensors(pairs, norm):
+    import torch
+    mu_in, sd_in, mu_out, sd_out = (torch.from_numpy(np.asarray(v, np.float64)).cuda() for v in norm)
+    X = (_features(pairs["y0"], pairs["T"], pairs["rho"], pairs["dt"]) - mu_in) / sd_in
+    D = (_targets(pairs["y0"], pairs["y1"]) - mu_out) / sd_out
+    return X.float().contiguous(), D.float().contiguous()
+
+
+def train(net: kt.Network, wl: I.Workload, n_pairs: int = 1_000_000, epochs: int = 4,
+          batch: int = 4096, lr: float = 2e-3, seed: int = 2504, val_pairs: int = 65536,
+          log=print) -> Dict[str, object]:
+    """Generate pairs with the solver and train a fresh MLP; returns the MLP and stats."""
+    import torch
+    t0 = time.perf_counter()
+    pairs = make_pairs(net, wl, n_pairs + val_pairs, seed)
+    t_data = time.perf_counter() - t0
+    n = pairs["T"].shape[0]
+    norm = normalisation({k: v[..., :n - val_pairs] for k, v in pairs.items()})
+    X, D = normalised_tensors(pairs, norm)
+    Xtr, Dtr, Xva, Dva = X[:n - val_pairs], D[:n - val_pairs], X[n - val_pairs:], D[n - val_pairs:]
+    mlp = kt.Mlp(net.ns + 3, net.n, seed=seed)
+    mlp.set_norm(*norm)
+    ntr = Xtr.shape[0]
+    steps = epochs * (ntr // batch)
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    t1 = time.perf_counter()
+    losses = []
+    k = 0
+    for ep in range(epochs):
+        perm = torch.randperm(ntr, device="cuda", generator=g)
+        for b in range(ntr // batch):
+            idx = perm[b * batch:(b + 1) * batch]
+            lr_k = lr * 0.5 * (1 + math.cos(math.pi * k / max(1, steps)))
+            want = (b == 0)
+            loss = mlp.train_step(Xtr[idx].contiguous(), Dtr[idx].contiguous(), lr_k, want_loss=want)
+            if want:
+                losses.append(loss)
+                log(f"epoch {ep} step {k} lr {lr_k:.2e} loss {loss:.4e}")
+            k += 1
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t1
+    pred = mlp.forward(Xva)[:, :net.n].double()
+    val = float(0.5 * ((pred - Dva[:, :net.n].double()) ** 2).sum(1).mean())
+    # relative error of the predicted end state vs the solver's, on held-out pairs
+    sd_out = torch.from_numpy(np.asarray(norm[3], np.float64)).cuda()[:net.n]
+    mu_out = torch.from_numpy(np.asarray(norm[2], np.float64)).cuda()[:net.n]
+    dlog_pred = mu_out + sd_out * pred
+    dlog_true = mu_out + sd_out * Dva[:, :net.n].double()
+    rel = torch.expm1((dlog_pred - dlog_true).abs()).max(dim=1).values
+    y0v = pairs["y0"][:, n - val_pairs:]
+    y1v = pairs["y1"][:, n - val_pairs:]
+    plain = ((y1v - y0v).abs() / torch.clamp(y1v.abs(), min=1e-300)).max(dim=0).values
+    return dict(mlp=mlp, norm=norm, val_loss=val, losses=losses, steps=k,
+                seconds_data=t_data, seconds_train=t_train, pairs=ntr,
+                guess_rel_err_median=float(rel.median()), plain_rel_err_median=float(plain.median()))
+
+
+def evaluate(net: kt.Network, wl: I.Workload, mlp: Optional[kt.Mlp], n_cells: int, seed: int,
+             form: int = kt.KT_FORM_FP64, dt_range=(1e-8, 1e-5)):
+    """Integrate fresh test cells over per-cell dt with and without the learned guess."""
+    import torch
+    y0, T = trajectory_states(net, wl, max(1, n_cells // 80), 80, seed)
+    y0, T = y0[:, :n_cells].contiguous(), T[:n_cells].contiguous()
+    g = torch.Generator(device="cpu").manual_seed(seed + 7)
+    u = torch.rand(n_cells, generator=g, dtype=torch.float64)
+    dt = torch.exp(math.log(dt_range[0]) + u * (math.log(dt_range[1]) - math.log(dt_range[0]))).cuda()
+    rho = torch.ones_like(T)
+    res = {}
+    if mlp is not None:
+        mlp.attach(net)
+    for name, guess in (("plain", kt.KT_GUESS_PREV), ("mlp", kt.KT_GUESS_MLP)):
+        if guess == kt.KT_GUESS_MLP and mlp is None:
+            continue
+        opts = kt.options(wl.tol, form=form, persistent=1, guess=guess)
+        kt.integrate_dt(net, y0, T, dt, opts)                       # warm-up
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        r = kt.integrate_dt(net, y0, T, dt, opts)
+        b.record()
+        kt.check_scratch(r["scratch"])
+        res[name] = dict(ms=a.elapsed_time(b), y=r["y"].cpu().numpy(), status=r["status"].cpu().numpy(),
+                         nsub=r["nsub"].cpu().numpy(), nnewton=r["nnewton"].cpu().numpy())
+    return dict(results=res, y0=y0.cpu().numpy(), T=T.cpu().numpy(), dt=dt.cpu().numpy())

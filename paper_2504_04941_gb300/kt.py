@@ -20,6 +20,7 @@ KT_FORM_FP64 = 0
 KT_FORM_FP32LU = 1
 KT_GUESS_PREV = 0
 KT_GUESS_MLP = 1
+KT_GUESS_FULLSTEP = 2
 STATUS_OK, STATUS_RETRIED, STATUS_REVERTED, STATUS_NONFINITE = 0, 1, 2, 3
 
 _lib = None
@@ -42,7 +43,8 @@ class Options(ctypes.Structure):
                 ("form", ctypes.c_int), ("guess", ctypes.c_int), ("persistent", ctypes.c_int),
                 ("retry", ctypes.c_int), ("atol_mode", ctypes.c_int),
                 ("block_warps", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
-                ("use_graph", ctypes.c_int), ("reserved", ctypes.c_int * 6)]
+                ("use_graph", ctypes.c_int), ("cells_per_warp", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 def lib():
@@ -73,6 +75,27 @@ def lib():
                                         ctypes.POINTER(Options), dptr, dptr, dptr, dptr, dptr,
                                         dptr, vp]
         L.kt_scratch_check.argtypes = [vp, vp]
+        L.kt_integrate_dt.argtypes = [vp, c_i64, dptr, dptr, dptr, dptr, ctypes.POINTER(Options),
+                                      dptr, dptr, dptr, dptr, dptr, dptr, vp]
+        L.kt_autotune.argtypes = [vp, c_i64, dptr, dptr, ctypes.c_double, ctypes.POINTER(Options),
+                                  dptr, dptr, dptr, vp, ctypes.POINTER(Options),
+                                  ctypes.POINTER(ctypes.c_double)]
+        fp = ctypes.POINTER(ctypes.c_float)
+        L.kt_mlp_sizes.argtypes = [ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
+        L.kt_mlp_create.argtypes = [c_int, c_int, ctypes.c_ulonglong, ctypes.POINTER(vp)]
+        L.kt_mlp_free.argtypes = [vp]
+        L.kt_mlp_free.restype = None
+        L.kt_mlp_set_norm.argtypes = [vp, fp, fp, fp, fp]
+        L.kt_mlp_train_step.argtypes = [vp, dptr, dptr, c_int, ctypes.c_float,
+                                        ctypes.POINTER(ctypes.c_double), vp]
+        L.kt_mlp_gradients.argtypes = [vp, dptr, dptr, c_int, fp, ctypes.POINTER(ctypes.c_double), vp]
+        L.kt_mlp_forward.argtypes = [vp, dptr, dptr, c_i64, vp]
+        L.kt_mlp_get_params.argtypes = [vp, fp]
+        L.kt_mlp_set_params.argtypes = [vp, fp]
+        L.kt_mlp_save.argtypes = [vp, ctypes.c_char_p]
+        L.kt_mlp_load_file.argtypes = [ctypes.c_char_p, ctypes.POINTER(vp)]
+        L.kt_mlp_load.argtypes = [vp, ctypes.c_char_p]
+        L.kt_network_attach_mlp.argtypes = [vp, vp]
         _lib = L
     return _lib
 
@@ -174,6 +197,29 @@ def integrate(net: Network, y, T, dt: float, opts: Options, rho=None, out=None,
     return dict(y=yo, T=To, status=st, nsub=nsub, nnewton=nnew, scratch=scratch)
 
 
+def integrate_dt(net: Network, y, T, dt_cells, opts: Options, out=None, scratch=None, stream=None):
+    """``integrate`` with a per-cell time step (CUDA float64 tensor [ncells])."""
+    import torch
+    ncells = T.shape[0]
+    dev = T.device
+    out = dict(out or {})
+    out.setdefault("y", torch.empty_like(y))
+    out.setdefault("T", torch.empty_like(T))
+    for k in ("status", "nsub", "nnewton"):
+        out.setdefault(k, torch.empty(ncells, dtype=torch.int32, device=dev))
+    if scratch is None:
+        scratch = torch.empty(scratch_bytes(), dtype=torch.uint8, device=dev)
+    for tns in (y, T, dt_cells, out["y"], out["T"]):
+        if tns.dtype != torch.float64 or not tns.is_contiguous() or not tns.is_cuda:
+            raise ValueError("y, T, dt_cells and outputs must be contiguous float64 CUDA tensors")
+    _check(lib().kt_integrate_dt(net.ptr, ncells, _ptr(y), _ptr(T), None, _ptr(dt_cells),
+                                 ctypes.byref(opts), _ptr(out["y"]), _ptr(out["T"]),
+                                 _ptr(out["status"]), _ptr(out["nsub"]), _ptr(out["nnewton"]),
+                                 _ptr(scratch), _stream_handle(stream)))
+    out["scratch"] = scratch
+    return out
+
+
 def scratch_bytes() -> int:
     return int(lib().kt_scratch_bytes())
 
@@ -235,3 +281,142 @@ def _np_ptr(a) -> Optional[int]:
     if not a.flags["C_CONTIGUOUS"]:
         raise ValueError("host arrays must be C-contiguous")
     return a.ctypes.data
+
+
+_TUNED_FIELDS = ("cells_per_warp", "persistent", "block_warps", "blocks_per_sm")
+
+
+def autotune(net: Network, y, T, dt: float, base: Options, stream=None):
+    """Search the launch configuration on a sample of cells held in CUDA tensors.
+
+    Returns (options, seconds of the best candidate on the sample)."""
+    import torch
+    yo, To = torch.empty_like(y), torch.empty_like(T)
+    scratch = torch.empty(scratch_bytes(), dtype=torch.uint8, device=T.device)
+    best = Options()
+    sec = ctypes.c_double()
+    _check(lib().kt_autotune(net.ptr, T.shape[0], _ptr(y), _ptr(T), float(dt), ctypes.byref(base),
+                             _ptr(yo), _ptr(To), _ptr(scratch), _stream_handle(stream),
+                             ctypes.byref(best), ctypes.byref(sec)))
+    return best, sec.value
+
+
+def tuned_options(net: Network, cells_y, cells_T, dt: float, base: Options, cache_path: str,
+                  sample: int = 4096):
+    """Options with the launch fields tuned for (network size, form, GPU), cached in a
+    JSON file; tunes on the first ``sample`` cells when the key is missing."""
+    import json
+    import torch
+    key = f"ns{net.ns}-nr{net.nr}-e{net.energy}-form{base.form}-{torch.cuda.get_device_name()}"
+    cache = {}
+    if os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+    opts = Options()
+    ctypes.memmove(ctypes.byref(opts), ctypes.byref(base), ctypes.sizeof(Options))
+    if key not in cache:
+        n = min(sample, cells_T.shape[0])
+        best, sec = autotune(net, cells_y[:, :n].contiguous(), cells_T[:n].contiguous(), dt, base)
+        cache[key] = {f: int(getattr(best, f)) for f in _TUNED_FIELDS}
+        cache[key]["sample_cells"] = n
+        cache[key]["sample_seconds"] = sec
+        tmp = cache_path + ".tmp"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, cache_path)
+    for f in _TUNED_FIELDS:
+        setattr(opts, f, cache[key][f])
+    return opts, cache[key]
+
+
+# ---------------------------------------------------------------- learned guess
+
+MLP_IN, MLP_HIDDEN, MLP_OUT = 16, 128, 8
+
+
+def mlp_layout():
+    """Offsets (floats) of the master parameters: W1 [128][16], W2, W3 [128][128],
+    W4 [8][128], b1, b2, b3 [128], b4 [8]."""
+    n = ctypes.c_int()
+    pb = ctypes.c_int()
+    _check(lib().kt_mlp_sizes(ctypes.byref(n), ctypes.byref(pb)))
+    shapes = [(MLP_HIDDEN, MLP_IN), (MLP_HIDDEN, MLP_HIDDEN), (MLP_HIDDEN, MLP_HIDDEN),
+              (MLP_OUT, MLP_HIDDEN), (MLP_HIDDEN,), (MLP_HIDDEN,), (MLP_HIDDEN,), (MLP_OUT,)]
+    offs, o = [], 0
+    for sh in shapes:
+        offs.append((o, sh))
+        o += int(np.prod(sh))
+    assert o == n.value
+    return offs, n.value
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+class Mlp:
+    """kt_mlp handle: n_in -> 128 -> 128 -> 128 -> n_out, BF16 weights, FP32 accumulate."""
+
+    def __init__(self, n_in: int = 0, n_out: int = 0, seed: int = 0, path: Optional[str] = None):
+        self.ptr = ctypes.c_void_p()
+        if path is not None:
+            _check(lib().kt_mlp_load_file(path.encode(), ctypes.byref(self.ptr)))
+        else:
+            _check(lib().kt_mlp_create(int(n_in), int(n_out), int(seed), ctypes.byref(self.ptr)))
+        self.n_in, self.n_out = n_in, n_out
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                lib().kt_mlp_free(self.ptr)
+                self.ptr = None
+        except Exception:
+            pass
+
+    def set_norm(self, mu_in, sd_in, mu_out, sd_out):
+        arrs = [np.ascontiguousarray(x, np.float32) for x in (mu_in, sd_in, mu_out, sd_out)]
+        _check(lib().kt_mlp_set_norm(self.ptr, *[_fp(x) for x in arrs]))
+
+    def train_step(self, X, Tg, lr: float, want_loss: bool = False, stream=None):
+        loss = ctypes.c_double()
+        _check(lib().kt_mlp_train_step(self.ptr, _ptr(X), _ptr(Tg), X.shape[0], float(lr),
+                                       ctypes.byref(loss) if want_loss else None,
+                                       _stream_handle(stream)))
+        return loss.value if want_loss else None
+
+    def gradients(self, X, Tg, stream=None):
+        _, n = mlp_layout()
+        g = np.zeros(n, np.float32)
+        loss = ctypes.c_double()
+        _check(lib().kt_mlp_gradients(self.ptr, _ptr(X), _ptr(Tg), X.shape[0], _fp(g),
+                                      ctypes.byref(loss), _stream_handle(stream)))
+        return g, loss.value
+
+    def forward(self, X, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty((X.shape[0], MLP_OUT), dtype=torch.float32, device=X.device)
+        _check(lib().kt_mlp_forward(self.ptr, _ptr(X), _ptr(out), X.shape[0], _stream_handle(stream)))
+        return out
+
+    def params(self):
+        _, n = mlp_layout()
+        p = np.zeros(n, np.float32)
+        _check(lib().kt_mlp_get_params(self.ptr, _fp(p)))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        _check(lib().kt_mlp_set_params(self.ptr, _fp(p)))
+
+    def save(self, path: str):
+        _check(lib().kt_mlp_save(self.ptr, path.encode()))
+
+    def attach(self, net: Network):
+        """Use this MLP for KT_GUESS_MLP integrations of ``net`` (keep self alive)."""
+        _check(lib().kt_network_attach_mlp(net.ptr, self.ptr))
+        net._mlp = self
+
+
+def state_load_mlp(state: "State", path: str):
+    _check(lib().kt_mlp_load(state.ptr, path.encode()))

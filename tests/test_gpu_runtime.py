@@ -1,0 +1,91 @@
+"""Runtime around the kernels: CUDA-graph replay, the launch autotuner, device errors."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_2504_04941_gb300 import inputs as I
+from _parity import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2504_04941_gb300 import build, kt as ktm
+    build.build()
+    return ktm
+
+
+def _direct(kt, net, cells, dt, opts):
+    import torch
+    y = torch.from_numpy(cells.y).cuda()
+    T = torch.from_numpy(cells.T).cuda()
+    r = kt.integrate(net, y, T, dt, opts)
+    kt.check_scratch(r["scratch"])
+    return {k: r[k].cpu().numpy() for k in ("y", "T", "status", "nsub", "nnewton")}
+
+
+@pytest.mark.parametrize("wid,n", [(1, 300), (2, 96), (3, 40)])
+def test_graph_replay_matches_direct(kt, wid, n):
+    wl = I.workload(wid, n)
+    net = kt.Network(wl.network)
+    st = kt.State(net, n)
+    for form in (0, 1):
+        opts = kt.options(wl.tol, form=form, persistent=1, use_graph=1)
+        ref = _direct(kt, net, wl.cells, wl.tol.dt, opts)
+        for rep in range(3):          # capture once, replay twice
+            st.upload(wl.cells.y, wl.cells.T, wl.cells.rho)
+            st.integrate(wl.tol.dt, opts)
+            out = st.download()
+            for k in ref:
+                assert np.array_equal(out[k], ref[k]), (form, rep, k)
+        # a different dt re-captures
+        st.upload(wl.cells.y, wl.cells.T, wl.cells.rho)
+        st.integrate(wl.tol.dt * 0.5, opts)
+        out = st.download()
+        ref2 = _direct(kt, net, wl.cells, wl.tol.dt * 0.5, opts)
+        for k in ref2:
+            assert np.array_equal(out[k], ref2[k]), (form, "dt", k)
+
+
+def test_autotune_and_cache(kt, oracle_mod, tmp_path):
+    import torch
+    wl = I.workload(2, 256)
+    net = kt.Network(wl.network)
+    y = torch.from_numpy(wl.cells.y).cuda()
+    T = torch.from_numpy(wl.cells.T).cuda()
+    base = kt.options(wl.tol, form=1)
+    best, sec = kt.autotune(net, y, T, wl.tol.dt, base)
+    assert best.cells_per_warp in (1, 32) and best.block_warps in (1, 2, 4, 8) and sec > 0
+    assert best.form == 1 and best.rtol == base.rtol
+    cache = str(tmp_path / "tuned.json")
+    opts, entry = kt.tuned_options(net, y, T, wl.tol.dt, base, cache, sample=128)
+    assert os.path.exists(cache) and len(json.load(open(cache))) == 1
+    opts2, _ = kt.tuned_options(net, y, T, wl.tol.dt, base, cache)   # cached: no re-tune
+    assert opts2.block_warps == opts.block_warps
+    g = _direct(kt, net, wl.cells, wl.tol.dt, opts)
+    o = oracle_mod.OracleNetwork(wl.network).integrate(wl.cells, wl.tol.dt, oracle_mod.options(wl.tol),
+                                                       os.cpu_count())
+    assert compare(g, o, 1).ok()
+
+
+def test_bad_arguments_are_errors_not_faults(kt):
+    import torch
+    wl = I.workload(1, 8)
+    net = kt.Network(wl.network)
+    y = torch.from_numpy(wl.cells.y).cuda()
+    T = torch.from_numpy(wl.cells.T).cuda()
+    with pytest.raises(kt.KtError):
+        kt.integrate(net, y, T, -1.0, kt.options(wl.tol))
+    with pytest.raises(kt.KtError):
+        kt.integrate(net, y, T, 1.0, kt.options(wl.tol, max_newton=0))
+    big = kt.Network(I.network(5))
+    with pytest.raises(kt.KtError):           # 65 unknowns cannot use one cell per lane
+        kt.integrate(big, torch.zeros((64, 4), dtype=torch.float64, device="cuda"),
+                     torch.full((4,), 1000.0, dtype=torch.float64, device="cuda"), 1e-9,
+                     kt.options(wl.tol, cells_per_warp=32))
