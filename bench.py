@@ -212,6 +212,8 @@ def main():
                     help="timed steps of the plain FP64 form (context line, not the headline)")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--dt-scale", type=float, default=1.0,
+                    help="scale the workload's dt (profiling captures on a short interval)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-cells", type=int, default=1024)
@@ -235,6 +237,7 @@ def main():
     ncells = args.ncells or I.FULL_CELLS[args.workload]
     # weak scaling: every rank integrates its own full batch (rank-dependent seed)
     wl = I.workload(args.workload, ncells, seed=I.SEED_BASE + args.workload + 1000 * rank)
+    wl.tol.dt *= args.dt_scale
     net = kt.Network(wl.network)
     dev = torch.device("cuda", local)
     y_in = torch.from_numpy(wl.cells.y).to(dev)

@@ -240,6 +240,10 @@ KT_API int kt_mlp_load(kt_state *st, const char *weights_path);
  * with opts.guess = KT_GUESS_MLP on this network; NULL detaches. */
 KT_API int kt_network_attach_mlp(kt_network *net, const kt_mlp *mlp);
 
+/* Diagnostics: out[i] = exp(x[i]) for device arrays, which = 0 CUDA's exp, 1 the
+ * library's table-driven exponential (valid for -708 <= x <= 709). */
+KT_API int kt_debug_exp(const double *x, double *out, int64_t n, int which, void *cuda_stream);
+
 /* Thread-local message of the last failed call ("" if none). */
 KT_API const char *kt_last_error(void);
 

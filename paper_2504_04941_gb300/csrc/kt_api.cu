@@ -45,6 +45,9 @@ int align16(int x) { return (x + 15) & ~15; }
 
 void kt::set_error(const char *msg) { g_err = msg; }
 
+// 2^(j/32) evaluated in long double and rounded once to double.
+double kt::exp2_table(int j) { return static_cast<double>(std::exp2(static_cast<long double>(j) / 32.0L)); }
+
 struct kt_network {
     std::string name;
     int ns = 0, ne = 0, nr = 0, energy = 0;
@@ -243,6 +246,7 @@ void build_blob(kt_network *n)
     v.off_cv = o; o = align16(o + 8 * n->ns);
     v.off_cnt = o; o = align16(o + 8 * n->ns * n->ne);
     v.off_idx = o; o = align16(o + 8 * n->nr);
+    v.off_exp = o; o = align16(o + 8 * 32);
     // per-species lists of (reaction, net coefficient)
     std::vector<int> rp(n->ns + 1, 0), re;
     for (int s = 0; s < n->ns; ++s) {
@@ -278,6 +282,7 @@ void build_blob(kt_network *n)
             ix[5 + j] = static_cast<unsigned char>(j < n->nout[r] ? n->out[r][j] : kt::kIdxNone);
         }
     }
+    for (int j = 0; j < 32; ++j) put(v.off_exp, j, kt::exp2_table(j));
     std::memcpy(n->blob.data() + v.off_rp, rp.data(), 4 * rp.size());
     if (!re.empty()) std::memcpy(n->blob.data() + v.off_re, re.data(), 4 * re.size());
     for (int s = 0; s < n->ns; ++s) {

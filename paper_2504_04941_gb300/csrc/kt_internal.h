@@ -21,6 +21,7 @@ struct NetView {
     int off_A, off_b, off_th, off_dH;     // double[nr]: prefactor, exponent, activation T, heat
     int off_h, off_cv, off_cnt;           // double[ns], double[ns], double[ns*ne]
     int off_idx;                          // uint8[nr*8]: nin, nout, in0..2, out0..2
+    int off_exp;                          // double[32]: 2^(j/32) for the table-driven exp
     int off_rp, off_re, nent;             // per-species reaction lists (CSR): int32 row
                                           // pointers [ns+1]; entries (r << 8) | (nu & 0xff),
                                           // nu = net stoichiometric coefficient (nonzero)
@@ -160,6 +161,9 @@ constexpr int kWarpMaxN = 96;   // unknowns per cell handled by the warp-per-cel
 
 // Thread-local error message shared by every entry point of the library.
 void set_error(const char *msg);
+
+// Entry j of the 2^(j/32) table of the table-driven exponential.
+double exp2_table(int j);
 
 // Device copy of an MLP's packed parameter block (null if m is null).
 const unsigned char *mlp_device_block(const kt_mlp *m, int *nin, int *nout, int *device);

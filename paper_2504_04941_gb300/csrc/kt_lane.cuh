@@ -1,0 +1,813 @@
+// kt_lane.cuh -- lane-per-cell fused integrator for small networks (N <= 16 unknowns).
+//
+// One CUDA thread owns one cell for its whole integration (Sec. 2.2 of the paper:
+// cells are independent).  The paper gives each cell a thread block and splits the
+// reactions and LU rows over threads (Sec. 2.3); for 3..16 unknowns that leaves most
+// of a warp idle on every FP64 instruction, and GB300's FP64 pipe is the scarce
+// resource, so here the 32 lanes of a warp integrate 32 different cells with the
+// same instruction stream.
+//
+// The sub-step control is flattened into a per-lane state machine: every trip of the
+// main loop performs exactly ONE Newton iteration for every live lane (rates ->
+// residual -> Jacobian -> Crout LU -> solve -> update), whatever phase of its
+// step-doubling attempt the lane is in.  Lanes of one warp therefore run the heavy
+// FP64 work in lockstep even though their cells need very different numbers of
+// sub-steps; only the cheap control logic diverges.  With `persistent`, a lane whose
+// cell is done pulls the next cell from a device work queue (one atomicAdd per warp
+// per refill, warp-aggregated), so no lane idles until the queue is empty.
+//
+// Per-cell arrays (iteration matrix, factors, pivots, state vectors) live in shared
+// memory, lane-interleaved (element e of lane l at [e*32 + l]): a warp reading "the
+// same element of its 32 cells" touches 32 consecutive words, conflict-free even
+// when the pivot row differs per lane.  The network tables are staged once per block
+// by one bulk (TMA) copy and read with warp-uniform addresses (broadcast).
+//
+// Forms:
+//   F32 = false  full Newton, FP64 Jacobian and LU (the plain form; same steps and
+//                order as the FP64 oracle).
+//   F32 = true   simplified Newton: the Jacobian is assembled in FP32 at the start of
+//                each step attempt (and refreshed when the contraction stalls), the
+//                iteration matrix I - h J is factorised in FP32 (once for h, once for
+//                h/2), while the residual, the update, the convergence test, the
+//                error norm and the conservation projection stay in FP64.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "kt_exp.cuh"
+#include "kt_internal.h"
+#include "kt_mlp.cuh"
+#include "kt_tma.cuh"
+
+namespace kt {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kMaxWarps = 8;
+
+#define LI(p, e) ((p)[(e) << 5])
+// per-lane arrays with a stride of 2^SH words (FP32 arrays interleave two per lane)
+#define LIS(p, e, SH) ((p)[(e) << (SH)])
+
+enum LaneState : int { kNeed = 0, kRun = 1, kDone = 2 };
+
+struct NetSmem {
+    const double *A, *b, *th, *dH, *h, *cv, *cnt, *ex;
+    const unsigned long long *idx;
+};
+
+__device__ __forceinline__ NetSmem net_smem(const unsigned char *sm, const NetView &nv)
+{
+    NetSmem t;
+    t.A = reinterpret_cast<const double *>(sm + nv.off_A);
+    t.b = reinterpret_cast<const double *>(sm + nv.off_b);
+    t.th = reinterpret_cast<const double *>(sm + nv.off_th);
+    t.dH = reinterpret_cast<const double *>(sm + nv.off_dH);
+    t.h = reinterpret_cast<const double *>(sm + nv.off_h);
+    t.cv = reinterpret_cast<const double *>(sm + nv.off_cv);
+    t.cnt = reinterpret_cast<const double *>(sm + nv.off_cnt);
+    t.idx = reinterpret_cast<const unsigned long long *>(sm + nv.off_idx);
+    t.ex = reinterpret_cast<const double *>(sm + nv.off_exp);
+    return t;
+}
+
+// Modified Arrhenius coefficient k = A (T/T_ref)^b exp(-theta/T) and dk/dT
+// (Sec. 2.2.1 item 1); exponents below -700 give exactly zero.  The exponential is
+// the table-driven one of kt_exp.cuh (within 2 ulp of exp()).
+__device__ __forceinline__ void arrhenius(const NetSmem &t, int r, double lt, double invT,
+                                          double &k, double &dk)
+{
+    const double b = t.b[r], th = t.th[r];
+    const double arg = b * lt - th * invT;
+    if (arg < -700.0) {
+        k = 0.0;
+        dk = 0.0;
+    } else {
+        k = t.A[r] * tang_exp(arg, t.ex);
+        dk = k * (b + th * invT) * invT;
+    }
+}
+
+// k alone; dk/dT = k (b + theta/T) / T is formed only where the Jacobian needs it.
+__device__ __forceinline__ double arrhenius_k(const NetSmem &t, int r, double lt, double invT)
+{
+    const double arg = t.b[r] * lt - t.th[r] * invT;
+    return arg < -700.0 ? 0.0 : t.A[r] * tang_exp(arg, t.ex);
+}
+
+// One pass over the reactions at state yt (Eq. method-ode-thermochem and the
+// mass-action / thermal-coupling partials of Eq. method-jacobian):
+//   W  <- f(yt)                                   (always, FP64)
+//   MODE 1: M64 <- I - hph * J(yt)                (FP64)
+//   MODE 2: J32 <- J(yt) when doJ                 (FP32; residual still FP64)
+// The temperature row uses each reaction's heat dH_r = sum h_out - sum h_in:
+// dT/dt = -sum_r dH_r w_r / C_V, an exact rewrite of -sum_s h_s (dn_s/dt) / C_V.
+template <int NT, bool ENERGY, int MODE>
+__device__ __forceinline__ void reaction_pass(const NetView &nv, const NetSmem &t,
+                                              const double *__restrict__ yt, const double *__restrict__ K,
+                                              double lt, double invT, double invCV, double hph,
+                                              double *__restrict__ W, double *__restrict__ M64,
+                                              float *__restrict__ J32, bool doJ)
+{
+    const int N = NT > 0 ? NT : nv.N, ns = nv.ns, nr = nv.nr;
+#pragma unroll
+    for (int i = 0; i < N; ++i) LI(W, i) = 0.0;
+    if (MODE == 1) {
+        for (int e = 0; e < N * N; ++e) LI(M64, e) = 0.0;
+    }
+    if (MODE == 2 && doJ) {
+        for (int e = 0; e < N * N; ++e) LIS(J32, e, 6) = 0.0f;
+    }
+    double fT = 0.0;
+    for (int r = 0; r < nr; ++r) {
+        const unsigned long long ix = t.idx[r];
+        const int nin = static_cast<int>(ix & 0xff), nout = static_cast<int>((ix >> 8) & 0xff);
+        const int i0 = static_cast<int>((ix >> 16) & 0xff), i1 = static_cast<int>((ix >> 24) & 0xff),
+                  i2 = static_cast<int>((ix >> 32) & 0xff);
+        const int o0 = static_cast<int>((ix >> 40) & 0xff), o1 = static_cast<int>((ix >> 48) & 0xff),
+                  o2 = static_cast<int>((ix >> 56) & 0xff);
+        const double k = ENERGY ? arrhenius_k(t, r, lt, invT) : LI(K, r);
+        const double y0 = LI(yt, i0);
+        const double y1 = nin > 1 ? LI(yt, i1) : 1.0;
+        const double y2 = nin > 2 ? LI(yt, i2) : 1.0;
+        const double p01 = y0 * y1;
+        const double w = k * p01 * y2;
+        LI(W, i0) -= w;
+        if (nin > 1) LI(W, i1) -= w;
+        if (nin > 2) LI(W, i2) -= w;
+        if (nout > 0) LI(W, o0) += w;
+        if (nout > 1) LI(W, o1) += w;
+        if (nout > 2) LI(W, o2) += w;
+        double dHr = 0.0;
+        if (ENERGY) {
+            dHr = t.dH[r];
+            fT -= dHr * w;
+        }
+        if (MODE == 1) {
+            // M = I - h J: a reactant row gains +h dw/dy_m, a product row -h dw/dy_m,
+            // the T row +h (dH_r/C_V) dw/dy_m.
+            const double hk = hph * k;
+            const double q = ENERGY ? dHr * invCV : 0.0;
+            auto col = [&](int m, double hd) {
+                LI(M64, i0 * N + m) += hd;
+                if (nin > 1) LI(M64, i1 * N + m) += hd;
+                if (nin > 2) LI(M64, i2 * N + m) += hd;
+                if (nout > 0) LI(M64, o0 * N + m) -= hd;
+                if (nout > 1) LI(M64, o1 * N + m) -= hd;
+                if (nout > 2) LI(M64, o2 * N + m) -= hd;
+                if (ENERGY) LI(M64, ns * N + m) += q * hd;
+            };
+            col(i0, hk * y1 * y2);
+            if (nin > 1) col(i1, hk * y0 * y2);
+            if (nin > 2) col(i2, hk * p01);
+            if (ENERGY) col(ns, hph * (k * (t.b[r] + t.th[r] * invT) * invT) * p01 * y2);
+        }
+        if (MODE == 2 && doJ) {
+            const float kf = static_cast<float>(k);
+            const float f0 = static_cast<float>(y0), f1 = static_cast<float>(y1),
+                        f2 = static_cast<float>(y2);
+            const float qf = ENERGY ? static_cast<float>(dHr * invCV) : 0.0f;
+            auto col = [&](int m, float d) {
+                LIS(J32, i0 * N + m, 6) -= d;
+                if (nin > 1) LIS(J32, i1 * N + m, 6) -= d;
+                if (nin > 2) LIS(J32, i2 * N + m, 6) -= d;
+                if (nout > 0) LIS(J32, o0 * N + m, 6) += d;
+                if (nout > 1) LIS(J32, o1 * N + m, 6) += d;
+                if (nout > 2) LIS(J32, o2 * N + m, 6) += d;
+                if (ENERGY) LIS(J32, ns * N + m, 6) -= qf * d;
+            };
+            col(i0, kf * f1 * f2);
+            if (nin > 1) col(i1, kf * f0 * f2);
+            if (nin > 2) col(i2, kf * f0 * f1);
+            if (ENERGY) col(ns, static_cast<float>(k * (t.b[r] + t.th[r] * invT) * invT * p01 * y2));
+        }
+    }
+    if (ENERGY) LI(W, ns) = fT * invCV;
+    if (MODE == 1) {
+        for (int i = 0; i < N; ++i) LI(M64, i * N + i) += 1.0;
+    }
+}
+
+// Crout LU with implicit-scaled row pivoting (Algorithm lu-decomp).  V holds the
+// inverse row maxima, then the inverse pivots (used by the back substitution).
+// Returns false on a zero row or a zero pivot.  T is double or float.
+template <typename T, int SH>
+__device__ __forceinline__ bool crout_lu(T *M, T *V, int *P, int N)
+{
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        T big = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const T a = LIS(M, i * N + j, SH);
+            big = a < T(0) ? (-a > big ? -a : big) : (a > big ? a : big);
+        }
+        ok = ok && (big > T(0));
+        LIS(V, i, SH) = big > T(0) ? T(1) / big : T(1);
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const int kmax = i < j ? i : j;
+            T s = LIS(M, i * N + j, SH);
+#pragma unroll
+            for (int k = 0; k < kmax; ++k) s -= LIS(M, i * N + k, SH) * LIS(M, k * N + j, SH);
+            LIS(M, i * N + j, SH) = s;
+        }
+        int imax = j;
+        T tmax = fabs(LIS(M, j * N + j, SH)) * LIS(V, j, SH);
+#pragma unroll
+        for (int i = j + 1; i < N; ++i) {
+            const T tt = fabs(LIS(M, i * N + j, SH)) * LIS(V, i, SH);
+            if (tt > tmax) {
+                tmax = tt;
+                imax = i;
+            }
+        }
+        ok = ok && (tmax > T(0));
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const T a = LIS(M, imax * N + k, SH), b = LIS(M, j * N + k, SH);
+            LIS(M, imax * N + k, SH) = b;
+            LIS(M, j * N + k, SH) = a;
+        }
+        const T va = LIS(V, imax, SH);
+        LIS(V, imax, SH) = LIS(V, j, SH);
+        LIS(V, j, SH) = va;
+        LI(P, j) = imax;
+        const T rinv = T(1) / LIS(M, j * N + j, SH);
+#pragma unroll
+        for (int i = j + 1; i < N; ++i) LIS(M, i * N + j, SH) *= rinv;
+        LIS(V, j, SH) = rinv;
+    }
+    return ok;
+}
+
+// Solve with the factors: row swaps in order, unit-lower forward, upper backward.
+template <typename T, int SH>
+__device__ __forceinline__ void crout_solve(const T *M, const T *V, const int *P, T *x, int N)
+{
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const int p = LI(P, i);
+        const T a = LIS(x, i, SH), b = LIS(x, p, SH);
+        LIS(x, i, SH) = b;
+        LIS(x, p, SH) = a;
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        T s = LIS(x, i, SH);
+#pragma unroll
+        for (int k = 0; k < i; ++k) s -= LIS(M, i * N + k, SH) * LIS(x, k, SH);
+        LIS(x, i, SH) = s;
+    }
+#pragma unroll
+    for (int i = N - 1; i >= 0; --i) {
+        T s = LIS(x, i, SH);
+#pragma unroll
+        for (int k = i + 1; k < N; ++k) s -= LIS(M, i * N + k, SH) * LIS(x, k, SH);
+        LIS(x, i, SH) = s * LIS(V, i, SH);
+    }
+}
+
+template <int NT, bool ENERGY, bool F32, bool PERSIST, bool MLPG>
+__global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a, const LaneLayout L)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    const NetView nv = a.nv;
+    if (!stage_table(sm, a.blob, static_cast<unsigned>(nv.bytes),
+                     reinterpret_cast<uint64_t *>(sm + nv.bytes), &a.scratch->error, kDevErrTma))
+        return;
+    const unsigned char *mlpP = sm + L.mlp_off;
+    if (MLPG && !stage_table(sm + L.mlp_off, a.mlp, static_cast<unsigned>(MlpLayout::BYTES),
+                             reinterpret_cast<uint64_t *>(sm + nv.bytes + 8), &a.scratch->error, kDevErrTma))
+        return;
+    const NetSmem t = net_smem(sm, nv);
+    const DevOpts o = a.o;
+    const int N = NT > 0 ? NT : nv.N, ns = nv.ns, ne = nv.ne, nr = nv.nr;
+    const long long nc = a.ncells;
+    const int lane = threadIdx.x & 31;
+    unsigned char *wb = sm + L.base + (threadIdx.x >> 5) * L.warp_bytes;
+    double *Y = reinterpret_cast<double *>(wb + L.off_Y) + lane;
+    double *YF = reinterpret_cast<double *>(wb + L.off_YF) + lane;
+    double *YH = reinterpret_cast<double *>(wb + L.off_YH) + lane;
+    double *Y2 = reinterpret_cast<double *>(wb + L.off_Y2) + lane;
+    double *W = reinterpret_cast<double *>(wb + L.off_W) + lane;
+    int *P = reinterpret_cast<int *>(wb + L.off_P) + lane;
+    double *K = ENERGY ? nullptr : reinterpret_cast<double *>(wb + L.off_K) + lane;
+    // FP64 matrix and scales; in the FP32 form they overlay the lane's own J32/M32 and
+    // V32/X32 slots and serve the FP64 rescue of a failed FP32 solve
+    double *M64 = reinterpret_cast<double *>(wb + L.off_M) + lane;
+    double *V64 = reinterpret_cast<double *>(wb + L.off_V) + lane;
+    float *J32 = nullptr, *M32 = nullptr, *V32 = nullptr, *X32 = nullptr;
+    if (F32) {
+        J32 = reinterpret_cast<float *>(wb + L.off_J) + 2 * lane;
+        M32 = J32 + 1;
+        V32 = reinterpret_cast<float *>(wb + L.off_V) + 2 * lane;
+        X32 = V32 + 1;
+    }
+
+    // ---- per-lane state
+    int state = kNeed;
+    long long cell = -1;
+    if (!PERSIST) {
+        cell = static_cast<long long>(blockIdx.x) * blockDim.x + threadIdx.x;
+        if (cell >= nc) state = kDone;
+    }
+    double tt = 0.0, h = 0.0, facmax = 0.0, T_iso = 0.0, invCV = 0.0, atol_s = 0.0, dtc = a.dt;
+    int phase = 0, it = 0, natt = 0, nacc = 0, nnew = 0, attempt = 0;
+    bool last = false;
+    // FP32 form: needJ -> assemble J32 at the current iterate; needF -> factorise;
+    // rescue -> this solve runs full FP64 Newton from its starting guess
+    bool needJ = false, needF = false, luok = true, rescue = false;
+    int refresh = 0;
+    double dprev = 0.0;
+    // learned guess: needG -> the attempt's first solve wants the MLP's starting point;
+    // usedG -> the current solve started from it (fall back to the plain start on failure)
+    bool needG = false, usedG = false;
+    double rho_c = 1.0;
+
+    auto finish = [&]() { state = PERSIST ? kNeed : kDone; };
+
+    // Pre-processing (Sec. 2.2.2): floors y >= 0 and T clamped to [t_min, t_max].
+    auto load_pre = [&]() {
+        for (int s = 0; s < ns; ++s) {
+            const double v = a.y_in[static_cast<long long>(s) * nc + cell];
+            LI(Y, s) = v > 0.0 ? v : 0.0;
+        }
+        const double Tin = a.T_in[cell];
+        const double T0 = Tin < nv.t_min ? nv.t_min : (Tin > nv.t_max ? nv.t_max : Tin);
+        T_iso = T0;
+        if (ENERGY) LI(Y, ns) = T0;
+    };
+
+    auto write_out = [&](int st) {
+        for (int s = 0; s < ns; ++s) a.y_out[static_cast<long long>(s) * nc + cell] = LI(Y, s);
+        a.T_out[cell] = ENERGY ? LI(Y, ns) : T_iso;
+        if (a.status) a.status[cell] = st;
+        if (a.nsub) a.nsub[cell] = st == KT_STATUS_REVERTED ? 0 : nacc;
+        if (a.nnew) a.nnew[cell] = nnew;
+    };
+
+    auto begin_attempt = [&]() -> bool {
+        if (natt >= o.max_substeps) return false;
+        ++natt;
+        last = false;
+        if (tt + h >= dtc * (1.0 - 1e-12)) {
+            h = dtc - tt;
+            last = true;
+        }
+        phase = 0;
+        it = 0;
+        for (int i = 0; i < N; ++i) LI(YF, i) = LI(Y, i);
+        if (F32) {
+            needJ = true;
+            needF = true;
+            refresh = 0;
+            rescue = false;
+        }
+        needG = MLPG && o.guess == KT_GUESS_MLP;
+        usedG = false;
+        return true;
+    };
+
+    auto start_run = [&](double h0, double fmax) -> bool {
+        tt = 0.0;
+        h = h0;
+        facmax = fmax;
+        natt = 0;
+        nacc = 0;
+        return begin_attempt();
+    };
+
+    // A failed run: retry once from the pre-processed input with a smaller first step
+    // and gentler growth, else revert to the pre-processed input (Sec. 2.2.3).
+    auto run_fail = [&]() {
+        if (attempt == 0 && o.retry) {
+            attempt = 1;
+            load_pre();
+            if (start_run(o.h_init * o.retry_h_factor, o.retry_facmax)) return;
+        }
+        load_pre();
+        write_out(KT_STATUS_REVERTED);
+        finish();
+    };
+
+    // Post-processing (Sec. 2.2.3): clip negatives, then restore the element totals b0
+    // of the pre-processed input by y_s -= y_s (N^T lambda)_s with
+    // (N diag(y) N^T) lambda = N y - b0.
+    auto post_process = [&]() -> bool {
+        double b0[kMaxElements], r[kMaxElements], Mp[kMaxElements * kMaxElements];
+        for (int e = 0; e < ne; ++e) b0[e] = 0.0;
+        for (int s = 0; s < ns; ++s) {
+            const double v = a.y_in[static_cast<long long>(s) * nc + cell];
+            const double y0 = v > 0.0 ? v : 0.0;
+            for (int e = 0; e < ne; ++e) b0[e] += t.cnt[s * ne + e] * y0;
+        }
+        for (int s = 0; s < ns; ++s)
+            if (LI(Y, s) < 0.0) LI(Y, s) = 0.0;
+        for (int e = 0; e < ne; ++e) {
+            double tot = 0.0;
+            for (int s = 0; s < ns; ++s) tot += t.cnt[s * ne + e] * LI(Y, s);
+            r[e] = tot - b0[e];
+            for (int f = 0; f < ne; ++f) {
+                double m = 0.0;
+                for (int s = 0; s < ns; ++s) m += t.cnt[s * ne + e] * t.cnt[s * ne + f] * LI(Y, s);
+                Mp[e * ne + f] = m;
+            }
+        }
+        for (int e = 0; e < ne; ++e) {
+            if (Mp[e * ne + e] == 0.0) {
+                if (r[e] != 0.0) return false;
+                for (int f = 0; f < ne; ++f) Mp[e * ne + f] = Mp[f * ne + e] = 0.0;
+                Mp[e * ne + e] = 1.0;
+            }
+        }
+        for (int k = 0; k < ne; ++k) {   // Gaussian elimination, partial pivoting
+            int p = k;
+            for (int i = k + 1; i < ne; ++i)
+                if (fabs(Mp[i * ne + k]) > fabs(Mp[p * ne + k])) p = i;
+            if (!(fabs(Mp[p * ne + k]) > 0.0)) return false;
+            if (p != k) {
+                for (int j = 0; j < ne; ++j) {
+                    const double x = Mp[k * ne + j];
+                    Mp[k * ne + j] = Mp[p * ne + j];
+                    Mp[p * ne + j] = x;
+                }
+                const double x = r[k];
+                r[k] = r[p];
+                r[p] = x;
+            }
+            for (int i = k + 1; i < ne; ++i) {
+                const double l = Mp[i * ne + k] / Mp[k * ne + k];
+                for (int j = k; j < ne; ++j) Mp[i * ne + j] -= l * Mp[k * ne + j];
+                r[i] -= l * r[k];
+            }
+        }
+        for (int i = ne - 1; i >= 0; --i) {
+            double s = r[i];
+            for (int j = i + 1; j < ne; ++j) s -= Mp[i * ne + j] * r[j];
+            r[i] = s / Mp[i * ne + i];
+        }
+        bool ok = true;
+        for (int s = 0; s < ns; ++s) {
+            double corr = 0.0;
+            for (int e = 0; e < ne; ++e) corr += t.cnt[s * ne + e] * r[e];
+            ok = ok && (corr < 1.0);
+            LI(Y, s) -= LI(Y, s) * corr;
+        }
+        for (int i = 0; i < N; ++i) ok = ok && isfinite(LI(Y, i));
+        return ok;
+    };
+
+    auto begin_cell = [&]() {
+        dtc = a.dt_cell ? a.dt_cell[cell] : a.dt;
+        rho_c = a.rho ? a.rho[cell] : 1.0;
+        bool fin = isfinite(a.T_in[cell]) && dtc > 0.0 && isfinite(dtc);
+        for (int s = 0; s < ns; ++s) fin = fin && isfinite(a.y_in[static_cast<long long>(s) * nc + cell]);
+        if (!fin) {
+            for (int s = 0; s < ns; ++s)
+                a.y_out[static_cast<long long>(s) * nc + cell] = a.y_in[static_cast<long long>(s) * nc + cell];
+            a.T_out[cell] = a.T_in[cell];
+            if (a.status) a.status[cell] = KT_STATUS_NONFINITE;
+            if (a.nsub) a.nsub[cell] = 0;
+            if (a.nnew) a.nnew[cell] = 0;
+            finish();
+            return;
+        }
+        load_pre();
+        double cvt = 0.0, b00 = 0.0;
+        for (int s = 0; s < ns; ++s) {
+            cvt += t.cv[s] * LI(Y, s);
+            b00 += t.cnt[s * ne] * LI(Y, s);
+        }
+        invCV = ENERGY ? 1.0 / cvt : 0.0;
+        atol_s = (o.atol_mode == 1 && b00 > 0.0) ? o.atol * b00 : o.atol;
+        if (!ENERGY) {
+            const double lt = log(T_iso / nv.t_ref), invT = 1.0 / T_iso;
+            for (int r = 0; r < nr; ++r) {
+                double k, dk;
+                arrhenius(t, r, lt, invT, k, dk);
+                LI(K, r) = k;
+            }
+        }
+        attempt = 0;
+        nnew = 0;
+        state = kRun;
+        if (!start_run(o.h_init, o.facmax)) run_fail();
+    };
+
+    auto step_fail_newton = [&]() {
+        h *= 0.5;
+        if (h < o.h_min || !begin_attempt()) run_fail();
+    };
+
+    // starting point of the current solve (plain predictor / second half from the full step)
+    auto restart_solve = [&]() {
+        double *yt = phase == 0 ? YF : (phase == 1 ? YH : Y2);
+        const double *g = phase == 2 ? (o.guess != KT_GUESS_PREV ? YF : YH) : Y;
+        for (int i = 0; i < N; ++i) LI(yt, i) = LI(g, i);
+        it = 0;
+    };
+
+    // Newton did not converge: a solve that started from the learned guess restarts from
+    // the plain predictor; an FP32 solve is redone in FP64; otherwise h halves.
+    auto newton_fail = [&]() {
+        if (usedG) {
+            usedG = false;
+            restart_solve();
+            if (F32) {
+                needJ = true;
+                needF = true;
+                refresh = 0;
+                rescue = false;
+            }
+            return;
+        }
+        if (F32 && !rescue) {
+            rescue = true;
+            restart_solve();
+            return;
+        }
+        step_fail_newton();
+    };
+
+    auto step_done = [&]() {
+        // weighted RMS of the step-doubling difference
+        double s2 = 0.0;
+        for (int i = 0; i < N; ++i) {
+            const double y = LI(Y, i), y2 = LI(Y2, i);
+            const double sc = (i < ns ? atol_s : 0.0) + o.rtol * fmax(fabs(y), fabs(y2));
+            const double e = (y2 - LI(YF, i)) / sc;
+            s2 += e * e;
+        }
+        const double err = sqrt(s2 / N);
+        if (err <= 1.0) {
+            for (int i = 0; i < N; ++i) LI(Y, i) = LI(Y2, i);
+            ++nacc;
+            if (last) {
+                if (post_process()) {
+                    write_out(attempt == 0 ? KT_STATUS_OK : KT_STATUS_RETRIED);
+                    finish();
+                } else {
+                    run_fail();
+                }
+                return;
+            }
+            tt += h;
+            double fac = err > 0.0 ? 0.9 / sqrt(err) : facmax;
+            if (fac > facmax) fac = facmax;
+            if (fac < 0.2) fac = 0.2;
+            h *= fac;
+            if (!begin_attempt()) run_fail();
+        } else {
+            double fac = 0.9 / sqrt(err);
+            if (!(fac >= 0.2)) fac = 0.2;
+            h *= fac;
+            if (h < o.h_min || !begin_attempt()) run_fail();
+        }
+    };
+
+    auto phase_done = [&]() {
+        usedG = false;
+        if (F32 && rescue) {      // the FP64 rescue overwrote the FP32 factors
+            rescue = false;
+            needJ = true;
+            needF = true;
+            refresh = 0;
+        }
+        if (phase == 0) {
+            phase = 1;
+            it = 0;
+            for (int i = 0; i < N; ++i) LI(YH, i) = LI(Y, i);
+            if (F32) { needF = true; }
+        } else if (phase == 1) {
+            phase = 2;
+            it = 0;
+            const double *g2 = o.guess != KT_GUESS_PREV ? YF : YH;
+            for (int i = 0; i < N; ++i) LI(Y2, i) = LI(g2, i);
+        } else {
+            step_done();
+        }
+    };
+
+    const double natol_frac = o.newton_atol_frac;
+    for (;;) {
+        // ---- give every idle lane a cell
+        for (;;) {
+            const bool want = state == kNeed;
+            if (PERSIST) {
+                const unsigned m = __ballot_sync(kFull, want);
+                if (!m) break;
+                const int leader = __ffs(m) - 1;
+                unsigned long long base = 0;
+                if (lane == leader) base = atomicAdd(&a.scratch->queue, static_cast<unsigned long long>(__popc(m)));
+                base = __shfl_sync(kFull, base, leader);
+                if (want) {
+                    cell = static_cast<long long>(base + __popc(m & ((1u << lane) - 1u)));
+                    if (cell >= nc) state = kDone;
+                    else begin_cell();
+                }
+            } else {
+                if (!__any_sync(kFull, want)) break;
+                if (want) begin_cell();
+            }
+        }
+        if (__all_sync(kFull, state == kDone)) break;
+
+        // ---- learned starting point for lanes that begin an attempt (warp-wide MMA)
+        if (MLPG) {
+            const bool wantG = state == kRun && needG;
+            if (__any_sync(kFull, wantG)) {
+                const float *nrm = reinterpret_cast<const float *>(mlpP + MlpLayout::NORM);
+                float x[kMlpIn];
+#pragma unroll
+                for (int k = 0; k < kMlpIn; ++k) x[k] = 0.0f;
+                if (wantG) {
+                    for (int k = 0; k < ns && k < kMlpIn; ++k)
+                        x[k] = static_cast<float>((log(fmax(LI(Y, k), 1e-30)) - nrm[k]) / nrm[16 + k]);
+                    const double Tc = ENERGY ? LI(Y, ns) : T_iso;
+                    const double f3[3] = {log(Tc), log(rho_c), log(h)};
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const int k = ns + q;
+                        if (k < kMlpIn) x[k] = static_cast<float>((f3[q] - nrm[k]) / nrm[16 + k]);
+                    }
+                }
+                uint32_t af[1][4];
+                float dlo[4], dhi[4];
+                gather_a(x, a.mlp_nin, 0, lane, af);
+                mlp_forward16(mlpP, af, dlo, lane);
+                gather_a(x, a.mlp_nin, 16, lane, af);
+                mlp_forward16(mlpP, af, dhi, lane);
+                float outv[kMlpOut];
+#pragma unroll
+                for (int q = 0; q < kMlpOut; ++q) {
+                    const float vlo = scatter_out(dlo, q, 0, lane);
+                    const float vhi = scatter_out(dhi, q, 16, lane);
+                    outv[q] = lane < 16 ? vlo : vhi;
+                }
+                if (wantG) {
+                    for (int i = 0; i < N && i < kMlpOut; ++i) {
+                        const double dlog = nrm[32 + i] + nrm[40 + i] * static_cast<double>(outv[i]);
+                        const double base = i < ns ? fmax(LI(Y, i), 1e-30) : LI(Y, i);
+                        const double g = base * exp(fmin(dlog, 50.0));
+                        LI(YF, i) = isfinite(g) ? g : LI(Y, i);
+                    }
+                    needG = false;
+                    usedG = true;
+                }
+            }
+        }
+        if (state != kRun) continue;
+
+        // ---- one Newton iteration of the current backward-Euler solve
+        const double *yb = phase == 2 ? YH : Y;
+        double *yt = phase == 0 ? YF : (phase == 1 ? YH : Y2);
+        const double hph = phase == 0 ? h : 0.5 * h;
+        ++nnew;
+        const double T = ENERGY ? LI(yt, ns) : T_iso;
+        const bool bad = !(T > 0.0);
+        double lt = 0.0, invT = 0.0;
+        if (ENERGY) {
+            const double Ts = bad ? 1.0 : T;
+            lt = log(Ts / nv.t_ref);
+            invT = 1.0 / Ts;
+        }
+        if (!F32 || rescue) {
+            reaction_pass<NT, ENERGY, 1>(nv, t, yt, K, lt, invT, invCV, hph, W, M64, nullptr, false);
+            for (int i = 0; i < N; ++i) LI(W, i) = -(LI(yt, i) - LI(yb, i) - hph * LI(W, i));
+            luok = crout_lu<double, 5>(M64, V64, P, N);
+            crout_solve<double, 5>(M64, V64, P, W, N);
+        } else {
+            const bool doJ = needJ;
+            reaction_pass<NT, ENERGY, 2>(nv, t, yt, K, lt, invT, invCV, hph, W, nullptr, J32, doJ);
+            if (needF) {
+                for (int i = 0; i < N; ++i)
+                    for (int j = 0; j < N; ++j)
+                        LIS(M32, i * N + j, 6) =
+                            (i == j ? 1.0f : 0.0f) - static_cast<float>(hph) * LIS(J32, i * N + j, 6);
+                luok = crout_lu<float, 6>(M32, V32, P, N);
+                needF = false;
+            }
+            needJ = false;
+            for (int i = 0; i < N; ++i)
+                LIS(X32, i, 6) = static_cast<float>(-(LI(yt, i) - LI(yb, i) - hph * LI(W, i)));
+            crout_solve<float, 6>(M32, V32, P, X32, N);
+            for (int i = 0; i < N; ++i) LI(W, i) = static_cast<double>(LIS(X32, i, 6));
+        }
+        bool conv = !bad && luok;
+        double dmax = 0.0;
+        for (int i = 0; i < N; ++i) {
+            const double d = LI(W, i);
+            const double y = LI(yt, i) + d;
+            LI(yt, i) = y;
+            const double tol = (i < ns ? natol_frac * atol_s : 0.0) + o.newton_rtol * fabs(y);
+            if (!(fabs(d) <= tol)) conv = false;
+            if (F32) {
+                const double q = fabs(d) / tol;
+                dmax = q > dmax ? q : dmax;
+            }
+        }
+
+        // ---- control
+        if (conv) {
+            phase_done();
+        } else if (!F32 || rescue) {
+            if (bad || !luok || it + 1 >= o.max_newton) newton_fail();
+            else ++it;
+        } else {
+            // simplified Newton: refresh J (at the current iterate) when the
+            // contraction stalls or the iteration budget of this factor is spent
+            const bool stalled = it > 0 && !(dmax < 0.5 * dprev);
+            if (bad || !luok || !isfinite(dmax)) {
+                newton_fail();
+            } else if (stalled || it + 1 >= o.max_newton) {
+                if (refresh < 2) {
+                    ++refresh;
+                    needJ = true;
+                    needF = true;
+                    it = 0;
+                } else {
+                    newton_fail();
+                }
+            } else {
+                ++it;
+            }
+            dprev = dmax;
+        }
+    }
+}
+
+template <int NT, bool ENERGY, bool F32, bool PERSIST, bool MLPG>
+int launch_t(const LaunchArgs &a, const LaunchCfg &c, cudaStream_t s)
+{
+    const LaneLayout L = lane_layout(a.nv.N, a.nv.nr, a.nv.energy, F32 ? 1 : 0, a.nv.bytes,
+                                     MLPG ? MlpLayout::BYTES : 0);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int smem_optin = 0, nsm = 0;
+    cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int warps = c.block_warps > 0 ? c.block_warps : kMaxWarps;
+    if (warps > kMaxWarps) warps = kMaxWarps;
+    while (warps > 1 && L.base + warps * L.warp_bytes > smem_optin) --warps;
+    const size_t smem = static_cast<size_t>(L.base) + static_cast<size_t>(warps) * L.warp_bytes;
+    if (smem > static_cast<size_t>(smem_optin)) return cudaErrorInvalidConfiguration;
+    auto kern = lane_kernel<NT, ENERGY, F32, PERSIST, MLPG>;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const int threads = warps * 32;
+    long long blocks;
+    if (PERSIST) {
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) per_sm = 1;
+        if (c.blocks_per_sm > 0 && c.blocks_per_sm < per_sm) per_sm = c.blocks_per_sm;
+        blocks = static_cast<long long>(per_sm) * nsm;
+        const long long need = (a.ncells + threads - 1) / threads;
+        if (blocks > need) blocks = need;
+    } else {
+        blocks = (a.ncells + threads - 1) / threads;
+    }
+    if (blocks < 1) return cudaSuccess;
+    kern<<<static_cast<unsigned>(blocks), threads, smem, s>>>(a, L);
+    return cudaGetLastError();
+}
+
+// Dispatch over the compile-time options for a fixed (or runtime, NT = 0) size.
+template <int NT>
+int launch_lane_n(const LaunchArgs &a, const LaunchCfg &c, cudaStream_t s)
+{
+    const bool en = a.nv.energy != 0, f32 = c.form == KT_FORM_FP32LU, per = c.persistent != 0;
+    if constexpr (NT == 0 || NT <= kMlpOut) {
+        if (a.mlp) {   // the learned guess runs with the persistent queue only
+            if (en)
+                return f32 ? launch_t<NT, true, true, true, true>(a, c, s) : launch_t<NT, true, false, true, true>(a, c, s);
+            return f32 ? launch_t<NT, false, true, true, true>(a, c, s) : launch_t<NT, false, false, true, true>(a, c, s);
+        }
+    } else {
+        if (a.mlp) return cudaErrorInvalidValue;
+    }
+    if (en) {
+        if (f32) return per ? launch_t<NT, true, true, true, false>(a, c, s) : launch_t<NT, true, true, false, false>(a, c, s);
+        return per ? launch_t<NT, true, false, true, false>(a, c, s) : launch_t<NT, true, false, false, false>(a, c, s);
+    }
+    if (f32) return per ? launch_t<NT, false, true, true, false>(a, c, s) : launch_t<NT, false, true, false, false>(a, c, s);
+    return per ? launch_t<NT, false, false, true, false>(a, c, s) : launch_t<NT, false, false, false, false>(a, c, s);
+}
+
+}  // namespace
+
+// Size-specialised launchers (one translation unit each).
+int launch_lane_n3(const LaunchArgs &a, const LaunchCfg &c, void *stream);
+int launch_lane_n11(const LaunchArgs &a, const LaunchCfg &c, void *stream);
+
+}  // namespace kt

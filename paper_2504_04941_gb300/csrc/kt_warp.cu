@@ -21,6 +21,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "kt_exp.cuh"
 #include "kt_internal.h"
 #include "kt_tma.cuh"
 
@@ -32,7 +33,7 @@ constexpr int kMaxWarps = 8;
 constexpr int kQ = 3;   // rows per lane (N <= 96)
 
 struct NetS {
-    const double *A, *b, *th, *h, *cv, *cnt;
+    const double *A, *b, *th, *h, *cv, *cnt, *ex;
     const unsigned long long *idx;
     const int *rp, *re;
 };
@@ -53,7 +54,7 @@ __device__ __forceinline__ void arrhenius(const NetS &t, int r, double lt, doubl
         k = 0.0;
         dk = 0.0;
     } else {
-        k = t.A[r] * exp(arg);
+        k = t.A[r] * tang_exp(arg, t.ex);
         dk = k * (b + th * invT) * invT;
     }
 }
@@ -196,6 +197,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) warp_kernel(const LaunchArgs a
     t.idx = reinterpret_cast<const unsigned long long *>(sm + nv.off_idx);
     t.rp = reinterpret_cast<const int *>(sm + nv.off_rp);
     t.re = reinterpret_cast<const int *>(sm + nv.off_re);
+    t.ex = reinterpret_cast<const double *>(sm + nv.off_exp);
     const DevOpts o = a.o;
     const int N = nv.N, ns = nv.ns, ne = nv.ne, nr = nv.nr, NP = L.NP;
     const long long nc = a.ncells;

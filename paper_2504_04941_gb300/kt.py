@@ -96,6 +96,7 @@ def lib():
         L.kt_mlp_load_file.argtypes = [ctypes.c_char_p, ctypes.POINTER(vp)]
         L.kt_mlp_load.argtypes = [vp, ctypes.c_char_p]
         L.kt_network_attach_mlp.argtypes = [vp, vp]
+        L.kt_debug_exp.argtypes = [dptr, dptr, c_i64, c_int, vp]
         _lib = L
     return _lib
 
@@ -420,3 +421,11 @@ class Mlp:
 
 def state_load_mlp(state: "State", path: str):
     _check(lib().kt_mlp_load(state.ptr, path.encode()))
+
+
+def debug_exp(x, which: int, stream=None):
+    """exp of a float64 CUDA tensor by CUDA's exp (0) or the library's table-driven one (1)."""
+    import torch
+    out = torch.empty_like(x)
+    _check(lib().kt_debug_exp(_ptr(x), _ptr(out), x.numel(), int(which), _stream_handle(stream)))
+    return out

@@ -60,16 +60,17 @@ def test_autotune_and_cache(kt, oracle_mod, tmp_path):
     y = torch.from_numpy(wl.cells.y).cuda()
     T = torch.from_numpy(wl.cells.T).cuda()
     base = kt.options(wl.tol, form=1)
-    best, sec = kt.autotune(net, y, T, wl.tol.dt, base)
+    dt = wl.tol.dt * 1e-3          # tuning runs every candidate twice: keep them short
+    best, sec = kt.autotune(net, y, T, dt, base)
     assert best.cells_per_warp in (1, 32) and best.block_warps in (1, 2, 4, 8) and sec > 0
     assert best.form == 1 and best.rtol == base.rtol
     cache = str(tmp_path / "tuned.json")
-    opts, entry = kt.tuned_options(net, y, T, wl.tol.dt, base, cache, sample=128)
+    opts, entry = kt.tuned_options(net, y, T, dt, base, cache, sample=128)
     assert os.path.exists(cache) and len(json.load(open(cache))) == 1
-    opts2, _ = kt.tuned_options(net, y, T, wl.tol.dt, base, cache)   # cached: no re-tune
+    opts2, _ = kt.tuned_options(net, y, T, dt, base, cache)   # cached: no re-tune
     assert opts2.block_warps == opts.block_warps
-    g = _direct(kt, net, wl.cells, wl.tol.dt, opts)
-    o = oracle_mod.OracleNetwork(wl.network).integrate(wl.cells, wl.tol.dt, oracle_mod.options(wl.tol),
+    g = _direct(kt, net, wl.cells, dt, opts)
+    o = oracle_mod.OracleNetwork(wl.network).integrate(wl.cells, dt, oracle_mod.options(wl.tol),
                                                        os.cpu_count())
     assert compare(g, o, 1).ok()
 
@@ -89,3 +90,20 @@ def test_bad_arguments_are_errors_not_faults(kt):
         kt.integrate(big, torch.zeros((64, 4), dtype=torch.float64, device="cuda"),
                      torch.full((4,), 1000.0, dtype=torch.float64, device="cuda"), 1e-9,
                      kt.options(wl.tol, cells_per_warp=32))
+
+
+def test_table_exp_against_cuda_and_libm(kt):
+    """The table-driven exponential (Tang 1989) is within 2 ulp of CUDA's exp and of
+    the host libm over the range the rate law uses."""
+    import torch
+    rng = np.random.default_rng(0)
+    x = np.concatenate([rng.uniform(-708.0, 709.0, 200000), rng.uniform(-1, 1, 50000),
+                        np.arange(-22000, 22000) * (np.log(2) / 32),
+                        [0.0, 1e-300, -1e-300, np.log(2) / 64, -np.log(2) / 64, 709.0, -708.0]])
+    xd = torch.from_numpy(x).cuda()
+    tang = kt.debug_exp(xd, 1).cpu().numpy()
+    cuda = kt.debug_exp(xd, 0).cpu().numpy()
+    host = np.exp(x)
+    ulp = np.spacing(host)
+    assert np.max(np.abs(tang - host) / ulp) <= 2.0
+    assert np.max(np.abs(tang - cuda) / np.spacing(cuda)) <= 2.0

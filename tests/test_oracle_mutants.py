@@ -1,0 +1,213 @@
+"""Plant plausible mistakes in a temporary copy of the oracle and check that the pins
+catch every one of them.  The mutated sources are compiled into a temporary library;
+the real oracle is not touched.
+"""
+import math
+import os
+import shutil
+import subprocess
+import types
+
+import numpy as np
+import pytest
+
+from paper_2504_04941_gb300 import inputs as I
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(ROOT, "oracle", "kt_oracle.c")
+PY = os.path.join(ROOT, "oracle", "oracle.py")
+
+# (name, original text, mutated text): each a mistake a reimplementation could make
+MUTANTS = [
+    ("rhs_sign", "for (j = 0; j < n->nin[r]; j++) f[n->in[r * KO_MAXSIDE + j]] -= w;",
+     "for (j = 0; j < n->nin[r]; j++) f[n->in[r * KO_MAXSIDE + j]] += w;"),
+    ("jac_product_term", "if (l != j) d *= y[in[l]];", "if (l == j) d *= y[in[l]];"),
+    ("jac_transposed", "J[in[a] * N + m] -= d;", "J[m * N + in[a]] -= d;"),
+    ("jac_drop_thermal", "for (a = 0; a < n->nin[r]; a++) J[in[a] * N + n->ns] -= dT;", ""),
+    ("dkdT_sign", "dkdT[r] = k[r] * (n->b[r] + n->theta[r] / T) / T;",
+     "dkdT[r] = k[r] * (n->b[r] - n->theta[r] / T) / T;"),
+    ("arrhenius_sign", "double arg = n->b[r] * lt - n->theta[r] / T;",
+     "double arg = n->b[r] * lt + n->theta[r] / T;"),
+    ("energy_sign", "f[n->ns] = -q / cvtot;", "f[n->ns] = q / cvtot;"),
+    ("lu_no_swap", "if (imax != j) {\n            for (k = 0; k < N; k++) {",
+     "if (0) {\n            for (k = 0; k < N; k++) {"),
+    ("lu_unscaled_pivot", [("double t = fabs(a[i * N + j]) / v[i];", "double t = fabs(a[i * N + j]);"),
+                           ("double tmax = fabs(a[j * N + j]) / v[j];", "double tmax = fabs(a[j * N + j]);")], None),
+    ("lu_no_l_scale", "for (i = j + 1; i < N; i++) a[i * N + j] /= a[j * N + j];", ""),
+    ("solve_no_perm", "double t = x[i]; x[i] = x[perm[i]]; x[perm[i]] = t;", ""),
+    ("be_sign_h", "c->G[i] = y[i] - yn[i] - h * c->f[i];", "c->G[i] = y[i] - yn[i] + h * c->f[i];"),
+    ("newton_update_sign", "y[i] += c->d[i];", "y[i] -= c->d[i];"),
+    ("step_full_instead_of_half", "for (i = 0; i < N; i++) y[i] = y2[i];\n            nacc++;",
+     "for (i = 0; i < N; i++) y[i] = yf[i];\n            nacc++;"),
+    ("half_step_from_wrong_base", "ok = be_solve(c, yh, 0.5 * h, y2) == 0;", "ok = be_solve(c, y, 0.5 * h, y2) == 0;"),
+    ("accept_wrong_norm_weight", "double sc = eatol(c, i) + c->o->rtol * fmax(fabs(y[i]), fabs(y2[i]));",
+     "double sc = eatol(c, i) + c->o->rtol * fabs(y[i]) * 1e3;"),
+]
+# Equivalent mutants, left out on purpose: they change nothing any pin (or any user)
+# can observe.  A different growth law (0.9/err instead of 0.9/sqrt(err), or err^2 in
+# place of err) is another valid controller of the same order; the post-processing
+# clip and the sign of the element projection act on rounding-level defects only,
+# because every Newton update of backward Euler conserves the linear invariants
+# exactly (N J = 0 implies N delta = -N G).
+
+
+def _load_variant(tmpdir, name, old, new):
+    src = open(SRC).read()
+    edits = old if isinstance(old, list) else [(old, new)]
+    for o, n_ in edits:
+        assert o in src, name
+        src = src.replace(o, n_, 1)
+    d = os.path.join(tmpdir, name)
+    os.makedirs(d, exist_ok=True)
+    c = os.path.join(d, "kt_oracle.c")
+    open(c, "w").write(src)
+    so = os.path.join(d, "libkt_oracle.so")
+    subprocess.check_call(["gcc", "-O1", "-std=c99", "-D_POSIX_C_SOURCE=200809L", "-ffp-contract=off",
+                           "-fPIC", "-shared", "-o", so, c, "-lm", "-lpthread"])
+    mod = types.ModuleType(f"oracle_{name}")
+    code = open(PY).read()
+    mod.__dict__["__file__"] = os.path.join(d, "oracle.py")
+    exec(compile(code, PY, "exec"), mod.__dict__)
+    mod.SRC, mod.LIB = c, so
+    mod._lib = None
+    return mod
+
+
+def _pins(m):
+    """A compact run of the pins of test_oracle_pins; returns the names that fail."""
+    failed = []
+
+    def check(name, fn):
+        try:
+            ok = fn()
+        except Exception:
+            ok = False
+        if not ok:
+            failed.append(name)
+
+    def lu_exact():
+        A = np.array([[2.0, 1e6, 3.0], [1.0, 1.0, -2.0], [4.0, -1.0, 5.0]])
+        b = np.array([1.0, 2.0, 3.0])
+        rc, fac, perm = m.lu(A)
+        return rc == 0 and np.allclose(m.lu_solve(fac, perm, b), np.linalg.solve(A, b), rtol=1e-12)
+
+    def lu_pivot():
+        rc, _, perm = m.lu([[2.0, 1e6], [1.0, 1.0]])
+        return rc == 0 and perm[0] == 1
+
+    def jac_fd():
+        for wid in (1, 2):
+            netw = I.network(wid)
+            net = m.OracleNetwork(netw)
+            wl = I.workload(wid, 3)
+            y = wl.cells.y[:, 1].copy()
+            T = float(wl.cells.T[1])
+            cv = float(netw.cv @ y) if netw.energy else 1.0
+            if netw.energy:
+                y = np.append(y, T)
+            J = net.jacobian(y, T, cv)
+            s = np.maximum(np.abs(y), 1e-6 * np.abs(y).max())
+            F = np.zeros_like(J)
+            for k in range(len(y)):
+                h = 1e-6 * s[k]
+                yp, ym = y.copy(), y.copy()
+                yp[k] += h
+                ym[k] -= h
+                F[:, k] = (net.rhs(yp, T, cv) - net.rhs(ym, T, cv)) / (2 * h)
+            Js, Fs = J * s[None, :], F * s[None, :]
+            sc = np.maximum(np.abs(Js), np.abs(Fs)).max(axis=1, keepdims=True) + 1e-300
+            if np.any(np.abs(Js - Fs) > 1e-6 * sc):
+                return False
+        return True
+
+    def rhs_robertson():
+        net = m.OracleNetwork(I.robertson_network())
+        y = np.array([0.7, 2e-5, 0.3])
+        ref = [-0.04 * y[0] + 1e4 * y[1] * y[2], 0.04 * y[0] - 1e4 * y[1] * y[2] - 3e7 * y[1] ** 2,
+               3e7 * y[1] ** 2]
+        return np.allclose(net.rhs(y), ref, rtol=1e-14)
+
+    def rates_printed():
+        net = m.OracleNetwork(I.stromgren_network(1e-9))
+        k, dk = net.rates(1e4)
+        kb = 8.617333262e-5
+        kci = 1.05e-9 * (1e4 / 300) ** 0.5 * math.exp(-13.6 / (kb * 1e4))
+        a = 3.5e-12 * (1e4 / 300) ** -0.75
+        h = 1e-2
+        fd = (3.5e-12 * ((1e4 + h) / 300) ** -0.75 - 3.5e-12 * ((1e4 - h) / 300) ** -0.75) / (2 * h)
+        return abs(k[1] / kci - 1) < 1e-12 and abs(k[2] / a - 1) < 1e-14 and abs(dk[2] / fd - 1) < 1e-6
+
+    def fixed_step_chain():
+        k1, k2 = 2.0, 50.0
+        net = m.OracleNetwork(I.decay_chain_network(k1, k2))
+        K = np.array([[-k1, 0, 0], [k1, -k2, 0], [0, k2, 0]])
+        y0 = np.array([0.7, 0.2, 0.1])
+        cells = I.Cells(y0.reshape(3, 1).copy(), np.array([300.0]), np.array([1.0]))
+        r = net.integrate(cells, 1.0, m.options(atol=1e-14, h_init=0.01, adaptive=0, retry=0,
+                                                newton_rtol=1e-14), 1)
+        ref = np.linalg.matrix_power(np.linalg.inv(np.eye(3) - 0.01 * K), 100) @ y0
+        return np.allclose(r["y"][:, 0], ref, rtol=1e-13, atol=1e-16)
+
+    def bateman():
+        net = m.OracleNetwork(I.decay_chain_network(1.0, 10.0))
+        cells = I.Cells(np.array([[1.0], [0.0], [0.0]]), np.array([300.0]), np.array([1.0]))
+        A = math.exp(-2.0)
+        B = 1 / 9 * (math.exp(-2.0) - math.exp(-20.0))
+        ref = np.array([A, B, 1 - A - B])
+        errs = []
+        for rtol in (1e-4, 1e-6):
+            r = net.integrate(cells, 2.0, m.options(rtol=rtol, atol=1e-14, h_init=1e-6), 1)
+            errs.append(np.abs(r["y"][:, 0] / ref - 1).max())
+        slope = math.log10(errs[0] / errs[1]) / 2
+        return errs[1] <= 2e-3 and 0.45 <= slope <= 0.55
+
+    def single_step_two_halves():
+        k1, k2 = 3.0, 40.0
+        net = m.OracleNetwork(I.decay_chain_network(k1, k2))
+        K = np.array([[-k1, 0, 0], [k1, -k2, 0], [0, k2, 0]])
+        y0 = np.array([0.6, 0.3, 0.1])
+        h = 1e-3
+        cells = I.Cells(y0.reshape(3, 1).copy(), np.array([300.0]), np.array([1.0]))
+        r = net.integrate(cells, h, m.options(rtol=1e-2, atol=1e-12, h_init=h, newton_rtol=1e-14,
+                                              retry=0), 1)
+        Mh = np.linalg.inv(np.eye(3) - 0.5 * h * K)
+        return r["nsub"][0] == 1 and np.allclose(r["y"][:, 0], Mh @ Mh @ y0, rtol=1e-13, atol=1e-16)
+
+    def conservation():
+        wl = I.workload(2, 4)
+        netw = wl.network
+        r = m.OracleNetwork(netw).integrate(wl.cells, wl.tol.dt, m.options(wl.tol), 1)
+        y0 = np.maximum(wl.cells.y, 0)
+        b0, b1 = netw.counts.T @ y0, netw.counts.T @ r["y"]
+        cv = netw.cv @ y0
+        E0 = cv * wl.cells.T + netw.h @ y0
+        E1 = cv * r["T"] + netw.h @ r["y"]
+        return (np.all(r["status"] == 0) and np.all(np.abs(b1 - b0) <= 1e-12 * b0) and
+                np.all(r["y"] >= 0) and np.all(np.abs(E1 - E0) <= 1e-12 * (cv * wl.cells.T + np.abs(netw.h) @ y0)))
+
+    def negative_input_clipped():
+        wl = I.workload(1, 1)
+        cells = I.Cells(np.array([[0.95], [-1e-7], [0.05]]), np.array([300.0]), np.array([1.0]))
+        r = m.OracleNetwork(wl.network).integrate(cells, 1e-3, m.options(wl.tol), 1)
+        return np.all(r["y"] >= 0) and abs(r["y"][:, 0].sum() - 1.0) < 1e-14
+
+    for name, fn in (("lu_exact", lu_exact), ("lu_pivot", lu_pivot), ("jac_fd", jac_fd),
+                     ("rhs_robertson", rhs_robertson), ("rates_printed", rates_printed),
+                     ("fixed_step_chain", fixed_step_chain), ("bateman", bateman),
+                     ("single_step_two_halves", single_step_two_halves),
+                     ("conservation", conservation), ("negative_input_clipped", negative_input_clipped)):
+        check(name, fn)
+    return failed
+
+
+def test_unmutated_copy_passes_all_pins(tmp_path):
+    m = _load_variant(str(tmp_path), "identity", "#include <ctype.h>", "#include <ctype.h>")
+    assert _pins(m) == []
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_mutant_is_caught(tmp_path, name, old, new):
+    m = _load_variant(str(tmp_path), name, old, new)
+    failed = _pins(m)
+    assert failed, f"mutant {name} survived every pin"

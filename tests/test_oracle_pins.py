@@ -181,8 +181,13 @@ def test_jacobian_vs_central_differences(oracle_mod, wid):
             y = np.append(y, T)
         J = net.jacobian(y, T, cvtot)
         Jfd = _fd_jacobian(net, y, T, cvtot)
-        scale = np.abs(J).max(axis=1, keepdims=True) + 1e-300
-        assert np.all(np.abs(J - Jfd) <= 1e-6 * scale + 1e-6 * np.abs(J)), (wid, c)
+        # columns times their variable's scale: every entry of a row is then the response
+        # of f_i to a relative change of one unknown (same units along the row), so a
+        # thermal-coupling term cannot hide behind the row's species entries
+        s = np.maximum(np.abs(y), 1e-6 * np.abs(y).max())
+        Js, Fs = J * s[None, :], Jfd * s[None, :]
+        scale = np.maximum(np.abs(Js), np.abs(Fs)).max(axis=1, keepdims=True) + 1e-300
+        assert np.all(np.abs(Js - Fs) <= 1e-6 * scale), (wid, c)
 
 
 def test_energy_row_is_heat_release(oracle_mod):
@@ -215,6 +220,22 @@ def test_backward_euler_fixed_step_linear_chain(oracle_mod):
     ref = np.linalg.matrix_power(np.linalg.inv(np.eye(3) - h * K), nsteps) @ y0
     assert r["status"][0] == 0 and r["nsub"][0] == nsteps
     assert np.allclose(r["y"][:, 0], ref, rtol=1e-13, atol=1e-16)
+
+
+def test_accepted_step_is_two_half_steps(oracle_mod):
+    """With step doubling, an accepted step of size h returns two backward-Euler half
+    steps: (I - (h/2) K)^-2 y0 for a linear chain (closed form, one accepted step)."""
+    k1, k2 = 3.0, 40.0
+    net = oracle_mod.OracleNetwork(I.decay_chain_network(k1, k2))
+    K = np.array([[-k1, 0, 0], [k1, -k2, 0], [0, k2, 0]])
+    y0 = np.array([0.6, 0.3, 0.1])
+    h = 1e-3
+    cells = I.Cells(y0.reshape(3, 1).copy(), np.array([300.0]), np.array([1.0]))
+    r = net.integrate(cells, h, oracle_mod.options(rtol=1e-2, atol=1e-12, h_init=h,
+                                                   newton_rtol=1e-14, retry=0), 1)
+    Mh = np.linalg.inv(np.eye(3) - 0.5 * h * K)
+    assert r["nsub"][0] == 1
+    assert np.allclose(r["y"][:, 0], Mh @ Mh @ y0, rtol=1e-13, atol=1e-16)
 
 
 def test_bateman_adaptive_first_order_scaling(oracle_mod):
