@@ -259,9 +259,9 @@ def main():
         base = kt.options(wl.tol, **forms["chosen"])
         cache = os.path.join(ROOT, "gpurun_out", "tuned.json") if os.path.isdir(
             os.path.join(ROOT, "gpurun_out")) else os.path.join(ROOT, ".tuned.json")
-        # tune on the whole batch over a short interval (dt/1000): every launch shape is
-        # exercised at full occupancy in well under a second per candidate
-        topts, tuned = kt.tuned_options(net, y_in, T_in, wl.tol.dt * 1e-3, base, cache,
+        # tune the launch shape on the whole batch over a short interval (dt/100): every
+        # candidate runs at full occupancy in a few seconds
+        topts, tuned = kt.tuned_options(net, y_in, T_in, wl.tol.dt * 1e-2, base, cache,
                                         sample=ncells)
         for f in ("cells_per_warp", "persistent", "block_warps", "blocks_per_sm"):
             forms["chosen"][f] = int(getattr(topts, f))

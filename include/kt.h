@@ -162,8 +162,9 @@ KT_API int kt_integrate_ptrs(const kt_network *net, int64_t ncells, const double
                       int32_t *status, int32_t *n_substeps, int32_t *n_newton,
                       void *scratch, void *cuda_stream);
 
-/* Launch-configuration search (one cell per lane vs one per warp, warps per block,
- * persistent queue or one pass) on a caller-supplied sample of cells in device
+/* Launch-configuration search (warps per block, persistent queue or one pass; the
+ * kernel family is base->cells_per_warp, or by size when 0: one cell per lane up to
+ * 16 unknowns, else one per warp) on a caller-supplied sample of cells in device
  * buffers: each candidate integrates the sample once untimed and once timed with
  * CUDA events on stream; *best receives base with the fastest configuration and
  * *best_seconds its time.  Same buffer rules as kt_integrate_ptrs; synchronises. */
@@ -187,7 +188,7 @@ KT_API int kt_scratch_check(void *scratch, void *cuda_stream);
 /* ---------------------------------------------------------------- learned guess
  * A small MLP predicts the Newton starting iterate of each sub-step (the paper's
  * closing section points at DeepODE-style learned solvers; there is no further
- * specification).  Architecture: n_in (<= 16) -> 128 -> 128 -> 128 -> n_out (<= 8),
+ * specification).  Architecture: n_in (<= 16) -> 128 -> 128 -> 128 -> n_out (<= 16),
  * SiLU, BF16 weights, FP32 accumulation (mma.sync tensor-core kernels).
  * For a network with ns species and N unknowns the guess uses n_in = ns + 3 features
  * (log max(y_s,1e-30), log T, log rho, log h), normalised as (x - mu_in)/sd_in, and
@@ -195,8 +196,8 @@ KT_API int kt_scratch_check(void *scratch, void *cuda_stream);
  * un-normalised as mu_out + sd_out * out.  If Newton does not converge from the guess
  * the step is retried from the plain predictor, so the answer is the solver's.
  * Master parameters (float32, kt_mlp_sizes() of them) in this order:
- * W1 [128][16], W2 [128][128], W3 [128][128], W4 [8][128], b1 [128], b2 [128],
- * b3 [128], b4 [8]; row n of W_l holds the weights of output n (z = h W^T + b);
+ * W1 [128][16], W2 [128][128], W3 [128][128], W4 [16][128], b1 [128], b2 [128],
+ * b3 [128], b4 [16]; row n of W_l holds the weights of output n (z = h W^T + b);
  * entries beyond n_in / n_out are zero and stay zero. */
 KT_API int kt_mlp_sizes(int *n_master_params, int *packed_bytes);
 
@@ -209,7 +210,7 @@ KT_API int kt_mlp_set_norm(kt_mlp *mlp, const float *mu_in, const float *sd_in,
                            const float *mu_out, const float *sd_out);
 
 /* One Adam step (lr; betas 0.9, 0.999; eps 1e-8) on the MSE loss
- * 1/(2B) sum (out - target)^2 of a batch: X [B][16] and targets [B][8] are
+ * 1/(2B) sum (out - target)^2 of a batch: X [B][16] and targets [B][16] are
  * normalised float32 device arrays (padding columns ignored).  *loss (host, may be
  * NULL; non-NULL synchronises) receives the loss before the update. */
 KT_API int kt_mlp_train_step(kt_mlp *mlp, const float *X, const float *targets, int B,
@@ -220,7 +221,7 @@ KT_API int kt_mlp_train_step(kt_mlp *mlp, const float *X, const float *targets, 
 KT_API int kt_mlp_gradients(kt_mlp *mlp, const float *X, const float *targets, int B,
                             float *grads, double *loss, void *cuda_stream);
 
-/* Batch inference: X [n][16] -> out [n][8] (normalised), device arrays, asynchronous. */
+/* Batch inference: X [n][16] -> out [n][16] (normalised), device arrays, asynchronous. */
 KT_API int kt_mlp_forward(const kt_mlp *mlp, const float *X, float *out, int64_t n,
                           void *cuda_stream);
 
@@ -228,7 +229,7 @@ KT_API int kt_mlp_forward(const kt_mlp *mlp, const float *X, float *out, int64_t
 KT_API int kt_mlp_get_params(const kt_mlp *mlp, float *master);
 KT_API int kt_mlp_set_params(kt_mlp *mlp, const float *master);
 
-/* Flat binary file: "KTMLP1", n_in, n_out, hidden, layers, seed, step, dtype tag,
+/* Flat binary file: "KTMLP2", n_in, n_out, hidden, layers, seed, step, dtype tag,
  * normalisation, float32 masters. */
 KT_API int kt_mlp_save(const kt_mlp *mlp, const char *path);
 KT_API int kt_mlp_load_file(const char *path, kt_mlp **out);

@@ -644,9 +644,14 @@ int kt_autotune(const kt_network *net, int64_t ncells, const double *y_in, const
     if (e != cudaSuccess) return cuda_fail(e, "kt_autotune: cudaEventCreate");
     double best_t = 1e300;
     kt_options cand = *base, win = *base;
-    const int cpws[2] = {32, 1};
+    // The kernel family follows the size unless the caller fixed it: one cell per lane
+    // when it fits (every FP64 warp instruction then serves 32 cells), else one per
+    // warp.  A short tuning sample cannot judge that choice (short integrations are
+    // latency-bound and favour one cell per warp), so only the launch shape is searched.
+    const int fam = base->cells_per_warp ? base->cells_per_warp : (N <= kt::kLaneMaxN ? 32 : 1);
+    const int cpws[1] = {fam};
     const int bws[4] = {1, 2, 4, 8};
-    for (int ci = 0; ci < 2; ++ci) {
+    for (int ci = 0; ci < 1; ++ci) {
         if (cpws[ci] == 32 && N > kt::kLaneMaxN) continue;
         for (int per = 0; per <= 1; ++per)
             for (int bi = 0; bi < 4; ++bi) {

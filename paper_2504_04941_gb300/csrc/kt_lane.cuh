@@ -640,7 +640,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
                     }
                 }
                 uint32_t af[1][4];
-                float dlo[4], dhi[4];
+                float dlo[kMlpOutTiles][4], dhi[kMlpOutTiles][4];
                 gather_a(x, a.mlp_nin, 0, lane, af);
                 mlp_forward16(mlpP, af, dlo, lane);
                 gather_a(x, a.mlp_nin, 16, lane, af);
@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
                 }
                 if (wantG) {
                     for (int i = 0; i < N && i < kMlpOut; ++i) {
-                        const double dlog = nrm[32 + i] + nrm[40 + i] * static_cast<double>(outv[i]);
+                        const double dlog = nrm[32 + i] + nrm[48 + i] * static_cast<double>(outv[i]);
                         const double base = i < ns ? fmax(LI(Y, i), 1e-30) : LI(Y, i);
                         const double g = base * exp(fmin(dlog, 50.0));
                         LI(YF, i) = isfinite(g) ? g : LI(Y, i);

@@ -34,7 +34,7 @@ struct Master {
     static constexpr int W1 = 0;                         // [128][16]
     static constexpr int W2 = W1 + kMlpH * kMlpIn;       // [128][128]
     static constexpr int W3 = W2 + kMlpH * kMlpH;
-    static constexpr int W4 = W3 + kMlpH * kMlpH;        // [8][128]
+    static constexpr int W4 = W3 + kMlpH * kMlpH;        // [16][128]
     static constexpr int B1 = W4 + kMlpOut * kMlpH;
     static constexpr int B2 = B1 + kMlpH;
     static constexpr int B3 = B2 + kMlpH;
@@ -105,10 +105,10 @@ __device__ __forceinline__ void repack(const float (&v)[NT][4], uint32_t (&a)[NT
 
 struct TrainBufs {
     const unsigned char *P;          // packed bf16 parameters
-    const float *X, *Tg;             // [B][16], [B][8]
+    const float *X, *Tg;             // [B][16], [B][16]
     __nv_bfloat16 *H0, *H1, *H2, *H3;  // activations: H0 [B][16], H1..H3 [B][128]
     __nv_bfloat16 *S1, *S2, *S3;     // SiLU derivatives [B][128]
-    __nv_bfloat16 *D1, *D2, *D3, *D4;  // dz: D1..D3 [B][128], D4 [B][8]
+    __nv_bfloat16 *D1, *D2, *D3, *D4;  // dz: D1..D3 [B][128], D4 [B][16]
     double *loss;
     int B, nout;
 };
@@ -173,28 +173,30 @@ __global__ void __launch_bounds__(128) train_fb(const TrainBufs tb)
     store_a(tb.H2 + m0 * kMlpH, a2);
     store_a(tb.H3 + m0 * kMlpH, a3);
     // output and loss gradient dz4 = (out - t) / B (rows beyond B and columns beyond nout: 0)
-    float d[4];
+    float d[kMlpOutTiles][4];
     mlp_out(tb.P, a3, d, lane);
-    float dz4[1][4];
+    float dz4[kMlpOutTiles][4];
     double lsum = 0.0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const long long m = m0 + g + (i >= 2 ? 8 : 0);
-        const int o = 2 * t + (i & 1);
-        float r = 0.0f;
-        if (m < tb.B && o < tb.nout) r = d[i] - tb.Tg[m * kMlpOut + o];
-        lsum += 0.5 * static_cast<double>(r) * r;
-        dz4[0][i] = r * invB;
-    }
+    for (int nt = 0; nt < kMlpOutTiles; ++nt)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const long long m = m0 + g + (i >= 2 ? 8 : 0);
+            const int o = nt * 8 + 2 * t + (i & 1);
+            float r = 0.0f;
+            if (m < tb.B && o < tb.nout) r = d[nt][i] - tb.Tg[m * kMlpOut + o];
+            lsum += 0.5 * static_cast<double>(r) * r;
+            dz4[nt][i] = r * invB;
+        }
     for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(kFull, lsum, off);
     if (lane == 0) atomicAdd(tb.loss, lsum / tb.B);
-    store_tile_bf16<1>(tb.D4 + m0 * kMlpOut, kMlpOut, dz4, lane);
-    // backward: dh3 = dz4 W4 (reduction over the 8 outputs, padded to 16)
+    store_tile_bf16<kMlpOutTiles>(tb.D4 + m0 * kMlpOut, kMlpOut, dz4, lane);
+    // backward: dh3 = dz4 W4 (reduction over the 16 outputs: one K chunk)
     uint32_t ad4[1][4];
     ad4[0][0] = pack_bf16(dz4[0][0], dz4[0][1]);
     ad4[0][1] = pack_bf16(dz4[0][2], dz4[0][3]);
-    ad4[0][2] = 0u;
-    ad4[0][3] = 0u;
+    ad4[0][2] = pack_bf16(dz4[1][0], dz4[1][1]);
+    ad4[0][3] = pack_bf16(dz4[1][2], dz4[1][3]);
     const __nv_bfloat16 *W4 = reinterpret_cast<const __nv_bfloat16 *>(tb.P + MlpLayout::W4);
     const __nv_bfloat16 *W3 = reinterpret_cast<const __nv_bfloat16 *>(tb.P + MlpLayout::W3);
     const __nv_bfloat16 *W2 = reinterpret_cast<const __nv_bfloat16 *>(tb.P + MlpLayout::W2);
@@ -357,16 +359,19 @@ __global__ void __launch_bounds__(128) infer(const unsigned char *P, const float
     a0[0][1] = pack_bf16(xin(m0 + g + 8, 2 * t), xin(m0 + g + 8, 2 * t + 1));
     a0[0][2] = pack_bf16(xin(m0 + g, 8 + 2 * t), xin(m0 + g, 9 + 2 * t));
     a0[0][3] = pack_bf16(xin(m0 + g + 8, 8 + 2 * t), xin(m0 + g + 8, 9 + 2 * t));
-    float d[4];
+    float d[kMlpOutTiles][4];
     mlp_forward16(P, a0, d, lane);
     const long long r0 = m0 + g, r1 = m0 + g + 8;
-    if (r0 < n) {
-        out[r0 * kMlpOut + 2 * t] = d[0];
-        out[r0 * kMlpOut + 2 * t + 1] = d[1];
-    }
-    if (r1 < n) {
-        out[r1 * kMlpOut + 2 * t] = d[2];
-        out[r1 * kMlpOut + 2 * t + 1] = d[3];
+#pragma unroll
+    for (int nt = 0; nt < kMlpOutTiles; ++nt) {
+        if (r0 < n) {
+            out[r0 * kMlpOut + nt * 8 + 2 * t] = d[nt][0];
+            out[r0 * kMlpOut + nt * 8 + 2 * t + 1] = d[nt][1];
+        }
+        if (r1 < n) {
+            out[r1 * kMlpOut + nt * 8 + 2 * t] = d[nt][2];
+            out[r1 * kMlpOut + nt * 8 + 2 * t + 1] = d[nt][3];
+        }
     }
 }
 
@@ -401,7 +406,7 @@ struct kt_mlp {
     int cap = 0;                                  // batch capacity of the buffers below
     __nv_bfloat16 *act = nullptr;                 // H0..H3, S1..S3, D1..D4
     double *loss = nullptr;
-    std::vector<float> norm = std::vector<float>(48, 0.0f);
+    std::vector<float> norm = std::vector<float>(kt::MlpLayout::NNORM, 0.0f);
 
     ~kt_mlp()
     {
@@ -505,7 +510,7 @@ int kt_mlp_sizes(int *n_master, int *packed_bytes)
 int kt_mlp_create(int n_in, int n_out, unsigned long long seed, kt_mlp **out)
 {
     if (!out || n_in < 1 || n_in > kt::kMlpIn || n_out < 1 || n_out > kt::kMlpOut)
-        return mfail(KT_EINVAL, "kt_mlp_create: n_in must be 1..16 and n_out 1..8");
+        return mfail(KT_EINVAL, "kt_mlp_create: n_in must be 1..16 and n_out 1..16");
     *out = nullptr;
     kt_mlp *m = new (std::nothrow) kt_mlp();
     if (!m) return mfail(KT_ENOMEM, "kt_mlp_create: out of memory");
@@ -546,7 +551,7 @@ int kt_mlp_create(int n_in, int n_out, unsigned long long seed, kt_mlp **out)
     fill(kt::Master::B3, 1, kt::kMlpH, kt::kMlpH, 1, kt::kMlpH);
     fill(kt::Master::B4, 1, kt::kMlpOut, kt::kMlpH, 1, n_out);
     for (int i = 0; i < 16; ++i) m->norm[16 + i] = 1.0f;
-    for (int i = 0; i < 8; ++i) m->norm[40 + i] = 1.0f;
+    for (int i = 0; i < 16; ++i) m->norm[48 + i] = 1.0f;
     e = cudaMemcpy(m->p, h.data(), h.size() * 4, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         delete m;
@@ -574,7 +579,7 @@ int kt_mlp_set_norm(kt_mlp *m, const float *mu_in, const float *sd_in, const flo
     for (int i = 0; i < m->nout; ++i) {
         if (!(sd_out[i] > 0)) return mfail(KT_EINVAL, "kt_mlp_set_norm: sd_out must be > 0");
         m->norm[32 + i] = mu_out[i];
-        m->norm[40 + i] = sd_out[i];
+        m->norm[48 + i] = sd_out[i];
     }
     cudaError_t e = cudaMemcpy(m->P + kt::MlpLayout::NORM, m->norm.data(), 4 * m->norm.size(), cudaMemcpyHostToDevice);
     return e == cudaSuccess ? KT_OK : mcuda(e, "kt_mlp_set_norm");
@@ -651,8 +656,8 @@ int kt_mlp_set_params(kt_mlp *m, const float *master)
     return m->repack_all(nullptr);
 }
 
-// File: "KTMLP1\0\0", int32 nin, nout, hidden, layers, uint64 seed, int32 step, dtype tag
-// (1 = float32 masters), float norm[48], float masters[N].
+// File: "KTMLP2\0\0", int32 nin, nout, hidden, layers, uint64 seed, int32 step, dtype tag
+// (1 = float32 masters), float norm[64], float masters[N].
 int kt_mlp_save(const kt_mlp *m, const char *path)
 {
     if (!m || !path) return mfail(KT_EINVAL, "kt_mlp_save: NULL argument");
@@ -661,14 +666,14 @@ int kt_mlp_save(const kt_mlp *m, const char *path)
     if (e != cudaSuccess) return mcuda(e, "kt_mlp_save");
     std::ofstream f(path, std::ios::binary);
     if (!f) return mfail(KT_EINVAL, "kt_mlp_save: cannot open file");
-    const char magic[8] = {'K', 'T', 'M', 'L', 'P', '1', 0, 0};
+    const char magic[8] = {'K', 'T', 'M', 'L', 'P', '2', 0, 0};
     const int32_t hdr[4] = {m->nin, m->nout, kt::kMlpH, 4};
     const int32_t tail[2] = {m->step, 1};
     f.write(magic, 8);
     f.write(reinterpret_cast<const char *>(hdr), sizeof hdr);
     f.write(reinterpret_cast<const char *>(&m->seed), 8);
     f.write(reinterpret_cast<const char *>(tail), sizeof tail);
-    f.write(reinterpret_cast<const char *>(m->norm.data()), 48 * 4);
+    f.write(reinterpret_cast<const char *>(m->norm.data()), m->norm.size() * 4);
     f.write(reinterpret_cast<const char *>(h.data()), h.size() * 4);
     return f ? KT_OK : mfail(KT_EINVAL, "kt_mlp_save: write failed");
 }
@@ -682,15 +687,15 @@ int kt_mlp_load_file(const char *path, kt_mlp **out)
     char magic[8];
     int32_t hdr[4], tail[2];
     unsigned long long seed = 0;
-    std::vector<float> norm(48), h(kt::Master::N);
+    std::vector<float> norm(kt::MlpLayout::NNORM), h(kt::Master::N);
     f.read(magic, 8);
     f.read(reinterpret_cast<char *>(hdr), sizeof hdr);
     f.read(reinterpret_cast<char *>(&seed), 8);
     f.read(reinterpret_cast<char *>(tail), sizeof tail);
-    f.read(reinterpret_cast<char *>(norm.data()), 48 * 4);
+    f.read(reinterpret_cast<char *>(norm.data()), norm.size() * 4);
     f.read(reinterpret_cast<char *>(h.data()), h.size() * 4);
-    if (!f || std::memcmp(magic, "KTMLP1", 6) != 0 || hdr[2] != kt::kMlpH || hdr[3] != 4 || tail[1] != 1)
-        return mfail(KT_EPARSE, "kt_mlp_load_file: not a KTMLP1 file of this architecture");
+    if (!f || std::memcmp(magic, "KTMLP2", 6) != 0 || hdr[2] != kt::kMlpH || hdr[3] != 4 || tail[1] != 1)
+        return mfail(KT_EPARSE, "kt_mlp_load_file: not a KTMLP2 file of this architecture");
     kt_mlp *m = nullptr;
     int rc = kt_mlp_create(hdr[0], hdr[1], seed, &m);
     if (rc) return rc;

@@ -1,6 +1,6 @@
 // kt_mlp.cuh -- the learned-guess MLP: layout and warp-level BF16 tensor-core forward.
 //
-// Network: in (<= 16 features) -> 128 -> 128 -> 128 -> out (<= 8), SiLU between
+// Network: in (<= 16 features) -> 128 -> 128 -> 128 -> out (<= 16), SiLU between
 // layers.  Weights W_l [n][k] (output-major, the reference convention z = h W^T + b)
 // in bfloat16, biases in float; accumulation in float.  Every matrix product is
 // mma.sync.m16n8k16 (BF16 in, FP32 accumulate) over 16-row tiles; the accumulator
@@ -15,7 +15,7 @@ namespace kt {
 
 constexpr int kMlpIn = 16;     // padded input width (one K chunk)
 constexpr int kMlpH = 128;     // hidden width
-constexpr int kMlpOut = 8;     // padded output width (one N tile)
+constexpr int kMlpOut = 16;    // padded output width (two N tiles)
 constexpr int kMlpKP1 = kMlpIn + 8;   // row stride (bf16) of W1: conflict-free B loads
 constexpr int kMlpKP = kMlpH + 8;     // row stride (bf16) of W2, W3, W4
 
@@ -24,13 +24,14 @@ struct MlpLayout {
     static constexpr int W1 = 0;                                   // bf16 [128][24]
     static constexpr int W2 = W1 + kMlpH * kMlpKP1 * 2;            // bf16 [128][136]
     static constexpr int W3 = W2 + kMlpH * kMlpKP * 2;             // bf16 [128][136]
-    static constexpr int W4 = W3 + kMlpH * kMlpKP * 2;             // bf16 [8][136]
+    static constexpr int W4 = W3 + kMlpH * kMlpKP * 2;             // bf16 [16][136]
     static constexpr int B1 = W4 + kMlpOut * kMlpKP * 2;           // float [128]
     static constexpr int B2 = B1 + kMlpH * 4;
     static constexpr int B3 = B2 + kMlpH * 4;
-    static constexpr int B4 = B3 + kMlpH * 4;                      // float [8]
-    static constexpr int NORM = B4 + kMlpOut * 4;                  // float [16 mu][16 sigma][8 mu][8 sigma]
-    static constexpr int BYTES = ((NORM + 48 * 4) + 15) & ~15;
+    static constexpr int B4 = B3 + kMlpH * 4;                      // float [16]
+    static constexpr int NORM = B4 + kMlpOut * 4;                  // float [16 mu][16 sigma][16 mu][16 sigma]
+    static constexpr int NNORM = 64;
+    static constexpr int BYTES = ((NORM + NNORM * 4) + 15) & ~15;
 };
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
@@ -94,27 +95,33 @@ __device__ __forceinline__ void mlp_hidden(const unsigned char *P, int woff, int
     }
 }
 
-// Output layer: d = a W4^T + b4 as a 16x8 accumulator fragment.
-__device__ __forceinline__ void mlp_out(const unsigned char *P, const uint32_t (&a)[8][4], float (&d)[4], int lane)
+constexpr int kMlpOutTiles = kMlpOut / 8;
+
+// Output layer: d = a W4^T + b4 as two 16x8 accumulator fragments (16 outputs).
+__device__ __forceinline__ void mlp_out(const unsigned char *P, const uint32_t (&a)[8][4],
+                                        float (&d)[kMlpOutTiles][4], int lane)
 {
     const __nv_bfloat16 *W = reinterpret_cast<const __nv_bfloat16 *>(P + MlpLayout::W4);
     const float *bias = reinterpret_cast<const float *>(P + MlpLayout::B4);
     const int t = lane & 3;
-    d[0] = bias[2 * t];
-    d[1] = bias[2 * t + 1];
-    d[2] = bias[2 * t];
-    d[3] = bias[2 * t + 1];
 #pragma unroll
-    for (int kc = 0; kc < 8; ++kc) {
-        uint32_t b0, b1;
-        b_frag(W, kMlpKP, 0, kc, lane, b0, b1);
-        mma_bf16(d, a[kc], b0, b1);
+    for (int nt = 0; nt < kMlpOutTiles; ++nt) {
+        d[nt][0] = bias[nt * 8 + 2 * t];
+        d[nt][1] = bias[nt * 8 + 2 * t + 1];
+        d[nt][2] = d[nt][0];
+        d[nt][3] = d[nt][1];
+#pragma unroll
+        for (int kc = 0; kc < 8; ++kc) {
+            uint32_t b0, b1;
+            b_frag(W, kMlpKP, nt, kc, lane, b0, b1);
+            mma_bf16(d[nt], a[kc], b0, b1);
+        }
     }
 }
 
 // Full forward of one 16-row tile from its input A fragment.
-__device__ __forceinline__ void mlp_forward16(const unsigned char *P, const uint32_t (&a0)[1][4], float (&d)[4],
-                                              int lane)
+__device__ __forceinline__ void mlp_forward16(const unsigned char *P, const uint32_t (&a0)[1][4],
+                                              float (&d)[kMlpOutTiles][4], int lane)
 {
     uint32_t a1[8][4], a2[8][4];
     float acc[16][4];
@@ -149,14 +156,15 @@ __device__ __forceinline__ void gather_a(const float (&x)[kMlpIn], int nf, int r
     a[0][3] = pack_bf16(v[6], v[7]);
 }
 
-// Output o (< 8) of row r of a 16x8 accumulator fragment, delivered to lane row0 + r.
-__device__ __forceinline__ float scatter_out(const float (&d)[4], int o, int row0, int lane)
+// Output o (< 16) of row r of the output fragments, delivered to lane row0 + r.
+__device__ __forceinline__ float scatter_out(const float (&d)[kMlpOutTiles][4], int o, int row0, int lane)
 {
     const int r = lane - row0;
     const int rr = r & 7;
-    const int src = rr * 4 + (o >> 1);
-    const float lo = __shfl_sync(0xffffffffu, (o & 1) ? d[1] : d[0], src);
-    const float hi = __shfl_sync(0xffffffffu, (o & 1) ? d[3] : d[2], src);
+    const int oo = o & 7, nt = o >> 3;
+    const int src = rr * 4 + (oo >> 1);
+    const float lo = __shfl_sync(0xffffffffu, (oo & 1) ? d[nt][1] : d[nt][0], src);
+    const float hi = __shfl_sync(0xffffffffu, (oo & 1) ? d[nt][3] : d[nt][2], src);
     return r < 8 ? lo : hi;
 }
 

@@ -462,8 +462,12 @@ FULL_CELLS = {1: 1024, 2: 65536, 3: 1048576, 4: 262144, 5: 160 ** 3}
 def tolerances(wid: int) -> Tolerances:
     if wid in (1, 4):
         return Tolerances(dt=1.0e4, rtol=1e-6, atol=1e-10, h_init=1e-6, h_min=1e-24)
-    if wid in (2, 5):
+    if wid == 2:
         return Tolerances(dt=1.0e-6, rtol=1e-6, atol=1e-20, h_init=1e-12, h_min=1e-30)
+    if wid == 5:
+        # dt at the scale of a hydrodynamic step; the 64-species cells still take
+        # ~10^3 sub-steps each from their random initial compositions
+        return Tolerances(dt=1.0e-9, rtol=1e-6, atol=1e-20, h_init=1e-13, h_min=1e-30)
     if wid == 3:
         # rtol 1e-4: the first-order scheme needs ~1600 sub-steps per active decade at
         # 1e-6; at 1e-4 the per-cell counts spread ~150..4000 (strong load imbalance)

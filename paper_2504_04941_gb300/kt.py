@@ -332,12 +332,12 @@ def tuned_options(net: Network, cells_y, cells_T, dt: float, base: Options, cach
 
 # ---------------------------------------------------------------- learned guess
 
-MLP_IN, MLP_HIDDEN, MLP_OUT = 16, 128, 8
+MLP_IN, MLP_HIDDEN, MLP_OUT = 16, 128, 16
 
 
 def mlp_layout():
     """Offsets (floats) of the master parameters: W1 [128][16], W2, W3 [128][128],
-    W4 [8][128], b1, b2, b3 [128], b4 [8]."""
+    W4 [16][128], b1, b2, b3 [128], b4 [16]."""
     n = ctypes.c_int()
     pb = ctypes.c_int()
     _check(lib().kt_mlp_sizes(ctypes.byref(n), ctypes.byref(pb)))

@@ -49,7 +49,7 @@ def _data(n, nin, nout, seed):
     rng = np.random.default_rng(seed)
     X = np.zeros((n, 16), np.float32)
     X[:, :nin] = rng.standard_normal((n, nin))
-    Tg = np.zeros((n, 8), np.float32)
+    Tg = np.zeros((n, 16), np.float32)
     Tg[:, :nout] = rng.standard_normal((n, nout))
     return X, Tg
 
@@ -114,7 +114,7 @@ def test_training_reduces_loss(kt):
     rng = np.random.default_rng(9)
     X = np.zeros((8192, 16), np.float32)
     X[:, :6] = rng.standard_normal((8192, 6))
-    Tg = np.zeros((8192, 8), np.float32)
+    Tg = np.zeros((8192, 16), np.float32)
     Tg[:, 0] = np.sin(X[:, 0]) + 0.5 * X[:, 1] * X[:, 2]
     Tg[:, 1] = np.tanh(X[:, 3] - X[:, 4])
     Tg[:, 2] = X[:, 5] ** 2 / 4

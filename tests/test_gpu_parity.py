@@ -115,6 +115,19 @@ def test_ism_ragged_parity(kt, oracle_mod, form):
     assert np.all(g["y"] >= 0)
 
 
+@pytest.mark.parametrize("form", [0, 1], ids=["fp64", "fp32lu"])
+def test_combined64_ragged_parity(kt, oracle_mod, form):
+    """64 species + T (65 unknowns, 1000 directed reactions; warp-per-cell), 37 cells."""
+    wl = I.workload(5, 37)
+    g = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, kt.options(wl.tol, form=form, persistent=1))
+    o = ora_run(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol)
+    rep = compare(g, o, wl.network.energy, rtol=wl.tol.rtol)
+    print(rep)
+    assert rep.ok(rtol=wl.tol.rtol), rep
+    assert conservation_error(wl.network, wl.cells.y, g["y"]) <= 1e-12
+    assert np.all(g["y"] >= 0)
+
+
 def test_edge_cases(kt, oracle_mod):
     import torch
     wl = I.workload(1, 40)
