@@ -182,6 +182,26 @@ KT_API int kt_integrate_dt(const kt_network *net, int64_t ncells, const double *
                            int32_t *status, int32_t *n_substeps, int32_t *n_newton,
                            void *scratch, void *cuda_stream);
 
+/* kt_integrate_ptrs for callers that must not allocate device memory (a host
+ * framework that owns every allocation, a step running inside a fixed memory pool or a
+ * real-time budget).  The paper has no counterpart; it is an interface of this library.
+ * The call allocates nothing: the work-queue counter, the device error word and the
+ * network tables live in one static device array of 64 KiB per device, held by every
+ * device that loads the library until the process exits.  Networks whose tables need
+ * more (256 bytes of counters plus the tables) are rejected with KT_EINVAL and a
+ * message.  The first call on a device looks up the array's device address (make that
+ * first call before any stream capture).  Every call shares the array and resets the
+ * counter and refreshes the tables itself; calls that overlap on the GPU (two streams,
+ * two host threads) race on it and must be ordered by the caller.  Same arguments and
+ * buffer rules as kt_integrate_ptrs except the scratch, which is internal; the
+ * learned guess is not available here (KT_EUNSUPPORTED).  Cells the kernels did not
+ * reach because of a device error keep status -1. */
+KT_API int kt_integrate_noalloc(const kt_network *net, int64_t ncells, const double *y_in,
+                                const double *T_in, const double *rho, double dt,
+                                const kt_options *opts, double *y_out, double *T_out,
+                                int32_t *status, int32_t *n_substeps, int32_t *n_newton,
+                                void *cuda_stream);
+
 /* Read and clear the device error word of a scratch buffer (synchronises stream). */
 KT_API int kt_scratch_check(void *scratch, void *cuda_stream);
 

@@ -456,6 +456,41 @@ int integrate_impl(const kt_network *net, int64_t ncells, const double *y_in, co
 
 }  // namespace
 
+int kt::prepare_launch(const kt_network *net, int64_t ncells, const double *y_in, const double *T_in,
+                       const double *rho, double dt, const kt_options *opts, double *y_out, double *T_out,
+                       int32_t *status, int32_t *n_substeps, int32_t *n_newton, kt::LaunchArgs *a,
+                       kt::LaunchCfg *c, const unsigned char **host_blob)
+{
+    if (!net) return fail(KT_EINVAL, "NULL network");
+    if (ncells < 0 || !(dt > 0) || !std::isfinite(dt)) return fail(KT_EINVAL, "bad ncells or dt");
+    int rc = check_opts(opts);
+    if (rc) return rc;
+    if (opts->guess == KT_GUESS_MLP) return fail(KT_EUNSUPPORTED, "the learned guess is not available here");
+    if (ncells > 0 && (!y_in || !T_in || !y_out || !T_out)) return fail(KT_EINVAL, "NULL device buffer");
+    const int N = net->ns + net->energy;
+    int cpw = opts->cells_per_warp;
+    if (cpw == 0) cpw = N <= kt::kLaneMaxN ? 32 : 1;
+    if ((cpw != 32 && cpw != 1) || (cpw == 32 && N > kt::kLaneMaxN))
+        return fail(KT_EINVAL, "cells_per_warp %d not available for %d unknowns", cpw, N);
+    if (N > kt::kWarpMaxN) return fail(KT_EUNSUPPORTED, "%d unknowns per cell; this build handles up to %d", N, kt::kWarpMaxN);
+    *a = kt::LaunchArgs{};
+    a->nv = net->view;
+    a->o = dev_opts(opts);
+    a->dt = dt;
+    a->rho = rho;
+    a->ncells = ncells;
+    a->y_in = y_in;
+    a->T_in = T_in;
+    a->y_out = y_out;
+    a->T_out = T_out;
+    a->status = status;
+    a->nsub = n_substeps;
+    a->nnew = n_newton;
+    *c = kt::LaunchCfg{opts->form, opts->persistent, opts->block_warps, opts->blocks_per_sm, cpw};
+    *host_blob = net->blob.data();
+    return KT_OK;
+}
+
 extern "C" {
 
 int kt_integrate_ptrs(const kt_network *net, int64_t ncells, const double *y_in, const double *T_in,

@@ -168,6 +168,14 @@ double exp2_table(int j);
 // Device copy of an MLP's packed parameter block (null if m is null).
 const unsigned char *mlp_device_block(const kt_mlp *m, int *nin, int *nout, int *device);
 
+// Launch arguments of an integrate call without its device tables and scratch (the
+// caller supplies both); validates like the allocating entry points.  Used by the
+// entry point that allocates nothing.
+int prepare_launch(const kt_network *net, int64_t ncells, const double *y_in, const double *T_in,
+                   const double *rho, double dt, const kt_options *opts, double *y_out, double *T_out,
+                   int32_t *status, int32_t *n_substeps, int32_t *n_newton, LaunchArgs *a, LaunchCfg *c,
+                   const unsigned char **host_blob);
+
 // Lane-per-cell kernels (N <= kLaneMaxN); returns a cudaError_t value.
 int launch_lane(const LaunchArgs &a, const LaunchCfg &c, void *stream);
 // Warp-per-cell kernels (N <= kWarpMaxN); returns a cudaError_t value.

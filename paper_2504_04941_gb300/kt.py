@@ -97,6 +97,8 @@ def lib():
         L.kt_mlp_load.argtypes = [vp, ctypes.c_char_p]
         L.kt_network_attach_mlp.argtypes = [vp, vp]
         L.kt_debug_exp.argtypes = [dptr, dptr, c_i64, c_int, vp]
+        L.kt_integrate_noalloc.argtypes = [vp, c_i64, dptr, dptr, dptr, ctypes.c_double,
+                                           ctypes.POINTER(Options), dptr, dptr, dptr, dptr, dptr, vp]
         _lib = L
     return _lib
 
@@ -428,4 +430,21 @@ def debug_exp(x, which: int, stream=None):
     import torch
     out = torch.empty_like(x)
     _check(lib().kt_debug_exp(_ptr(x), _ptr(out), x.numel(), int(which), _stream_handle(stream)))
+    return out
+
+
+def integrate_noalloc(net: Network, y, T, dt: float, opts: Options, out, rho=None, stream=None):
+    """kt_integrate_noalloc: the integrate call that allocates no device memory.
+
+    For callers that cannot allocate at the point of the call: the library keeps its
+    work-queue counter and the network tables in a fixed static device array, so the
+    caller passes inputs and preallocated outputs only (``out``: dict of CUDA tensors
+    y, T, status, nsub, nnewton).  Calls that overlap on the GPU race on that array."""
+    for k in ("y", "T"):
+        if out[k].dtype != y.dtype or not out[k].is_contiguous():
+            raise ValueError("outputs must be contiguous float64 CUDA tensors")
+    _check(lib().kt_integrate_noalloc(net.ptr, T.shape[0], _ptr(y), _ptr(T), _ptr(rho), float(dt),
+                                      ctypes.byref(opts), _ptr(out["y"]), _ptr(out["T"]),
+                                      _ptr(out.get("status")), _ptr(out.get("nsub")),
+                                      _ptr(out.get("nnewton")), _stream_handle(stream)))
     return out
