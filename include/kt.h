@@ -98,7 +98,12 @@ typedef struct {
     int use_graph;           /* 1: kt_integrate replays a captured CUDA graph    (0) */
     int cells_per_warp;      /* 32: one cell per lane (networks with <= 16 unknowns);
                                 1: one cell per warp (<= 96 unknowns); 0: automatic (0) */
-    int reserved[5];
+    int schedule;            /* kt_integrate on a state with persistent = 1: 1 hands
+                                out the cells with the most Newton iterations in the
+                                previous call first (the state's n_newton counters;
+                                zero after kt_state_create), 0 in index order.  The
+                                order changes no result, only the load balance (0) */
+    int reserved[4];
 } kt_options;
 
 /* Defaults listed above. */

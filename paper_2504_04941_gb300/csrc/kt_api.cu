@@ -114,6 +114,8 @@ struct kt_state {
     double g_dt = 0.0;
     kt_options g_opts{};
     kt_mlp *mlp = nullptr;                        // learned-guess MLP loaded for this state (owned)
+    int *order = nullptr;                         // longest-first queue order (opts.schedule)
+    unsigned *sched_work = nullptr;               // its histogram and cursors
 };
 
 namespace {
@@ -260,6 +262,9 @@ void build_blob(kt_network *n)
     }
     rp[n->ns] = static_cast<int>(re.size());
     v.nent = static_cast<int>(re.size());
+    v.shape = n->nr > 0 ? 22 : 0;
+    for (int r = 0; r < n->nr; ++r)
+        if (n->nin[r] != 2 || n->nout[r] != 2) v.shape = 0;
     v.off_rp = o; o = align16(o + 4 * (n->ns + 1));
     v.off_re = o; o = align16(o + 4 * v.nent);
     if (o < 16) o = 16;
@@ -394,7 +399,7 @@ namespace {
 int integrate_impl(const kt_network *net, int64_t ncells, const double *y_in, const double *T_in,
                    const double *rho, const double *dt_cell, double dt, const kt_options *opts, double *y_out,
                    double *T_out, int32_t *status, int32_t *n_substeps, int32_t *n_newton, void *scratch,
-                   void *cuda_stream, const kt_mlp *mlp)
+                   void *cuda_stream, const kt_mlp *mlp, const int *order = nullptr)
 {
     if (!net) return fail(KT_EINVAL, "kt_integrate: NULL network");
     if (ncells < 0 || !(dt > 0) || !std::isfinite(dt)) return fail(KT_EINVAL, "kt_integrate: bad ncells or dt");
@@ -448,6 +453,7 @@ int integrate_impl(const kt_network *net, int64_t ncells, const double *y_in, co
     a.nsub = n_substeps;
     a.nnew = n_newton;
     a.scratch = static_cast<kt::Scratch *>(scratch);
+    a.order = opts->persistent ? order : nullptr;
     kt::LaunchCfg c{opts->form, opts->persistent, opts->block_warps, opts->blocks_per_sm, cpw};
     int ce = cpw == 32 ? kt::launch_lane(a, c, cuda_stream) : kt::launch_warp(a, c, cuda_stream);
     if (ce != 0) return cuda_fail(static_cast<cudaError_t>(ce), "integrate kernel launch");
@@ -576,6 +582,8 @@ void kt_state_free(kt_state *st)
     cudaFree(st->nsub);
     cudaFree(st->nnew);
     cudaFree(st->scratch);
+    cudaFree(st->order);
+    cudaFree(st->sched_work);
     delete st;
 }
 
@@ -598,30 +606,68 @@ int kt_state_upload(kt_state *st, const double *y, const double *T, const double
     return KT_OK;
 }
 
+namespace {
+
+// Longest-first order of the state's cells from the Newton counts of the previous call
+// (opts.schedule with a persistent launch); buffers are allocated on first use, outside
+// any stream capture.  *order is null when the option is off.
+int state_schedule(kt_state *st, const kt_options *opts, cudaStream_t s, bool launch, const int **order)
+{
+    *order = nullptr;
+    if (!opts->schedule || !opts->persistent || st->ncells > 0x7fffffffLL) return KT_OK;
+    if (!st->order) {
+        cudaError_t e = cudaMalloc(&st->order, static_cast<size_t>(st->ncells) * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&st->sched_work, 2 * kt::kSchedBuckets * sizeof(unsigned));
+        if (e != cudaSuccess) return fail(KT_ENOMEM, "kt_integrate: schedule buffers: %s", cudaGetErrorString(e));
+    }
+    if (launch) {
+        const int ce = kt::launch_schedule(st->nnew, st->ncells, st->sched_work, st->order, s);
+        if (ce != 0) return cuda_fail(static_cast<cudaError_t>(ce), "schedule kernels");
+    }
+    *order = st->order;
+    return KT_OK;
+}
+
+}  // namespace
+
 int kt_integrate(kt_state *st, double dt, const kt_options *opts, void *cuda_stream)
 {
     if (!st) return fail(KT_EINVAL, "kt_integrate: NULL state");
-    if (!opts || !opts->use_graph || st->ncells == 0)
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (!opts || !opts->use_graph || st->ncells == 0) {
+        const int *order = nullptr;
+        if (opts && st->ncells > 0) {
+            int rc = check_opts(opts);
+            if (rc) return rc;
+            rc = state_schedule(st, opts, s, true, &order);
+            if (rc) return rc;
+        }
         return integrate_impl(st->net, st->ncells, st->y, st->T, st->rho, nullptr, dt, opts, st->y, st->T,
-                              st->status, st->nsub, st->nnew, st->scratch, cuda_stream, st->mlp);
+                              st->status, st->nsub, st->nnew, st->scratch, cuda_stream, st->mlp, order);
+    }
     int rc = check_opts(opts);
     if (rc) return rc;
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     if (st->gexec && st->g_dt == dt && std::memcmp(&st->g_opts, opts, sizeof(kt_options)) == 0) {
         cudaError_t e = cudaGraphLaunch(st->gexec, s);
         return e == cudaSuccess ? KT_OK : cuda_fail(e, "cudaGraphLaunch");
     }
-    // upload the network tables first: no synchronous call may run inside the capture
+    // upload the network tables and allocate the schedule buffers first: no
+    // synchronous call may run inside the capture
     const unsigned char *blob = nullptr;
     rc = const_cast<kt_network *>(st->net)->device_blob(&blob);
+    if (rc) return rc;
+    const int *order = nullptr;
+    rc = state_schedule(st, opts, s, false, &order);
     if (rc) return rc;
     cudaError_t e = cudaSuccess;
     if (!st->cap) e = cudaStreamCreateWithFlags(&st->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate(capture)");
     e = cudaStreamBeginCapture(st->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-    rc = integrate_impl(st->net, st->ncells, st->y, st->T, st->rho, nullptr, dt, opts, st->y, st->T,
-                        st->status, st->nsub, st->nnew, st->scratch, st->cap, st->mlp);
+    rc = state_schedule(st, opts, st->cap, true, &order);
+    if (!rc)
+        rc = integrate_impl(st->net, st->ncells, st->y, st->T, st->rho, nullptr, dt, opts, st->y, st->T,
+                            st->status, st->nsub, st->nnew, st->scratch, st->cap, st->mlp, order);
     cudaGraph_t g = nullptr;
     e = cudaStreamEndCapture(st->cap, &g);
     if (rc) {

@@ -25,6 +25,8 @@ struct NetView {
     int off_rp, off_re, nent;             // per-species reaction lists (CSR): int32 row
                                           // pointers [ns+1]; entries (r << 8) | (nu & 0xff),
                                           // nu = net stoichiometric coefficient (nonzero)
+    int shape;                            // 22: every reaction has 2 reactants and 2
+                                          // products (straight-line rate code); 0: mixed
     int bytes;                            // total, multiple of 16
     double t_ref, t_min, t_max;
 };
@@ -59,6 +61,7 @@ struct LaunchArgs {
     double *y_out, *T_out;
     int *status, *nsub, *nnew;
     Scratch *scratch;
+    const int *order;            // persistent queue order (device, may be null: index order)
 };
 
 struct LaunchCfg {
@@ -77,6 +80,7 @@ struct LaneLayout {
     int off_M, off_J, off_V, off_P, off_X;         // matrix / factor / scale / perm / fp32 rhs
     int off_Y, off_YF, off_YH, off_Y2, off_W;      // fp64 vectors
     int off_K;                                     // per-cell rate coefficients (isothermal)
+    int off_FY;                                    // fp32 form: f at the attempt's start state
     int warp_bytes;                                // bytes per warp
     int mlp_off;                                   // byte offset of the staged MLP block
     int base;                                      // byte offset of warp 0 (after blob, barriers, MLP)
@@ -110,6 +114,7 @@ inline LaneLayout lane_layout(int N, int nr, int energy, int fp32, int blob_byte
     L.off_YH = o; o += N * d;
     L.off_Y2 = o; o += N * d;
     L.off_W = o; o += N * d;
+    if (fp32) { L.off_FY = o; o += N * d; } else { L.off_FY = -1; }
     if (!energy) { L.off_K = o; o += nr * d; } else { L.off_K = -1; }
     L.warp_bytes = (o + 255) & ~255;
     L.mlp_off = (blob_bytes + 16 + 255) & ~255;
@@ -175,6 +180,12 @@ int prepare_launch(const kt_network *net, int64_t ncells, const double *y_in, co
                    const double *rho, double dt, const kt_options *opts, double *y_out, double *T_out,
                    int32_t *status, int32_t *n_substeps, int32_t *n_newton, LaunchArgs *a, LaunchCfg *c,
                    const unsigned char **host_blob);
+
+// Longest-first queue order from per-cell cost counts (kt_sched.cu): work holds
+// 2 * kSchedBuckets unsigned words, order receives a permutation of 0..ncells-1 with the
+// cells of the largest counts first.  Returns a cudaError_t value.
+constexpr int kSchedBuckets = 128;
+int launch_schedule(const int *count, long long ncells, unsigned *work, int *order, void *stream);
 
 // Lane-per-cell kernels (N <= kLaneMaxN); returns a cudaError_t value.
 int launch_lane(const LaunchArgs &a, const LaunchCfg &c, void *stream);

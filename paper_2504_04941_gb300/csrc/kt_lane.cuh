@@ -74,6 +74,14 @@ __device__ __forceinline__ NetSmem net_smem(const unsigned char *sm, const NetVi
     return t;
 }
 
+// x < -700 decided on the bit pattern (integer compare; same result as the FP64 compare
+// for every non-NaN x): negative and |x| > 700.0 (0x4085E00000000000).
+__device__ __forceinline__ bool below_m700(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b < 0 && (b & 0x7fffffffffffffffLL) > 0x4085E00000000000LL;
+}
+
 // Modified Arrhenius coefficient k = A (T/T_ref)^b exp(-theta/T) and dk/dT
 // (Sec. 2.2.1 item 1); exponents below -700 give exactly zero.  The exponential is
 // the table-driven one of kt_exp.cuh (within 2 ulp of exp()).
@@ -82,7 +90,7 @@ __device__ __forceinline__ void arrhenius(const NetSmem &t, int r, double lt, do
 {
     const double b = t.b[r], th = t.th[r];
     const double arg = b * lt - th * invT;
-    if (arg < -700.0) {
+    if (below_m700(arg)) {
         k = 0.0;
         dk = 0.0;
     } else {
@@ -95,8 +103,16 @@ __device__ __forceinline__ void arrhenius(const NetSmem &t, int r, double lt, do
 __device__ __forceinline__ double arrhenius_k(const NetSmem &t, int r, double lt, double invT)
 {
     const double arg = t.b[r] * lt - t.th[r] * invT;
-    return arg < -700.0 ? 0.0 : t.A[r] * tang_exp(arg, t.ex);
+    return below_m700(arg) ? 0.0 : t.A[r] * tang_exp(arg, t.ex);
 }
+
+// log(T / T_ref), skipping the division when T_ref is 1 (the same value bit for bit).
+__device__ __forceinline__ double log_t(double T, double t_ref)
+{
+    return log(t_ref == 1.0 ? T : T / t_ref);
+}
+
+constexpr int kChunk = 4;   // reactions whose rates are formed before their scatter
 
 // One pass over the reactions at state yt (Eq. method-ode-thermochem and the
 // mass-action / thermal-coupling partials of Eq. method-jacobian):
@@ -105,7 +121,12 @@ __device__ __forceinline__ double arrhenius_k(const NetSmem &t, int r, double lt
 //   MODE 2: J32 <- J(yt) when doJ                 (FP32; residual still FP64)
 // The temperature row uses each reaction's heat dH_r = sum h_out - sum h_in:
 // dT/dt = -sum_r dH_r w_r / C_V, an exact rewrite of -sum_s h_s (dn_s/dt) / C_V.
-template <int NT, bool ENERGY, int MODE>
+// Reactions go in chunks of kChunk: the rate coefficients and rates of a chunk are
+// independent FP64 chains formed first, then scattered in reaction order (the same
+// sums in the same order as one reaction at a time).  S2 = true when every reaction
+// is A + B -> C + D (straight-line code; multiplying by the absent third reactant's
+// 1.0 is exact, so the results are the same as the general code's).
+template <int NT, bool ENERGY, int MODE, bool S2>
 __device__ __forceinline__ void reaction_pass(const NetView &nv, const NetSmem &t,
                                               const double *__restrict__ yt, const double *__restrict__ K,
                                               double lt, double invT, double invCV, double hph,
@@ -115,6 +136,7 @@ __device__ __forceinline__ void reaction_pass(const NetView &nv, const NetSmem &
     const int N = NT > 0 ? NT : nv.N, ns = nv.ns, nr = nv.nr;
 #pragma unroll
     for (int i = 0; i < N; ++i) LI(W, i) = 0.0;
+    auto wadd = [&](int i, double v) { LI(W, i) += v; };
     if (MODE == 1) {
         for (int e = 0; e < N * N; ++e) LI(M64, e) = 0.0;
     }
@@ -122,67 +144,94 @@ __device__ __forceinline__ void reaction_pass(const NetView &nv, const NetSmem &
         for (int e = 0; e < N * N; ++e) LIS(J32, e, 6) = 0.0f;
     }
     double fT = 0.0;
-    for (int r = 0; r < nr; ++r) {
-        const unsigned long long ix = t.idx[r];
-        const int nin = static_cast<int>(ix & 0xff), nout = static_cast<int>((ix >> 8) & 0xff);
-        const int i0 = static_cast<int>((ix >> 16) & 0xff), i1 = static_cast<int>((ix >> 24) & 0xff),
-                  i2 = static_cast<int>((ix >> 32) & 0xff);
-        const int o0 = static_cast<int>((ix >> 40) & 0xff), o1 = static_cast<int>((ix >> 48) & 0xff),
-                  o2 = static_cast<int>((ix >> 56) & 0xff);
-        const double k = ENERGY ? arrhenius_k(t, r, lt, invT) : LI(K, r);
-        const double y0 = LI(yt, i0);
-        const double y1 = nin > 1 ? LI(yt, i1) : 1.0;
-        const double y2 = nin > 2 ? LI(yt, i2) : 1.0;
-        const double p01 = y0 * y1;
-        const double w = k * p01 * y2;
-        LI(W, i0) -= w;
-        if (nin > 1) LI(W, i1) -= w;
-        if (nin > 2) LI(W, i2) -= w;
-        if (nout > 0) LI(W, o0) += w;
-        if (nout > 1) LI(W, o1) += w;
-        if (nout > 2) LI(W, o2) += w;
-        double dHr = 0.0;
-        if (ENERGY) {
-            dHr = t.dH[r];
-            fT -= dHr * w;
+    for (int r0 = 0; r0 < nr; r0 += kChunk) {
+        unsigned long long ixq[kChunk];
+        double kq[kChunk], y0q[kChunk], y1q[kChunk], y2q[kChunk], wq[kChunk];
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+            const int r = r0 + q < nr ? r0 + q : nr - 1;
+            const unsigned long long ix = t.idx[r];
+            ixq[q] = ix;
+            const int nin = S2 ? 2 : static_cast<int>(ix & 0xff);
+            const int i0 = static_cast<int>((ix >> 16) & 0xff), i1 = static_cast<int>((ix >> 24) & 0xff),
+                      i2 = static_cast<int>((ix >> 32) & 0xff);
+            const double k = ENERGY ? arrhenius_k(t, r, lt, invT) : LI(K, r);
+            const double y0 = LI(yt, i0);
+            const double y1 = nin > 1 ? LI(yt, i1) : 1.0;
+            const double y2 = (!S2 && nin > 2) ? LI(yt, i2) : 1.0;
+            kq[q] = k;
+            y0q[q] = y0;
+            y1q[q] = y1;
+            y2q[q] = y2;
+            wq[q] = S2 ? k * (y0 * y1) : k * (y0 * y1) * y2;
         }
-        if (MODE == 1) {
-            // M = I - h J: a reactant row gains +h dw/dy_m, a product row -h dw/dy_m,
-            // the T row +h (dH_r/C_V) dw/dy_m.
-            const double hk = hph * k;
-            const double q = ENERGY ? dHr * invCV : 0.0;
-            auto col = [&](int m, double hd) {
-                LI(M64, i0 * N + m) += hd;
-                if (nin > 1) LI(M64, i1 * N + m) += hd;
-                if (nin > 2) LI(M64, i2 * N + m) += hd;
-                if (nout > 0) LI(M64, o0 * N + m) -= hd;
-                if (nout > 1) LI(M64, o1 * N + m) -= hd;
-                if (nout > 2) LI(M64, o2 * N + m) -= hd;
-                if (ENERGY) LI(M64, ns * N + m) += q * hd;
-            };
-            col(i0, hk * y1 * y2);
-            if (nin > 1) col(i1, hk * y0 * y2);
-            if (nin > 2) col(i2, hk * p01);
-            if (ENERGY) col(ns, hph * (k * (t.b[r] + t.th[r] * invT) * invT) * p01 * y2);
-        }
-        if (MODE == 2 && doJ) {
-            const float kf = static_cast<float>(k);
-            const float f0 = static_cast<float>(y0), f1 = static_cast<float>(y1),
-                        f2 = static_cast<float>(y2);
-            const float qf = ENERGY ? static_cast<float>(dHr * invCV) : 0.0f;
-            auto col = [&](int m, float d) {
-                LIS(J32, i0 * N + m, 6) -= d;
-                if (nin > 1) LIS(J32, i1 * N + m, 6) -= d;
-                if (nin > 2) LIS(J32, i2 * N + m, 6) -= d;
-                if (nout > 0) LIS(J32, o0 * N + m, 6) += d;
-                if (nout > 1) LIS(J32, o1 * N + m, 6) += d;
-                if (nout > 2) LIS(J32, o2 * N + m, 6) += d;
-                if (ENERGY) LIS(J32, ns * N + m, 6) -= qf * d;
-            };
-            col(i0, kf * f1 * f2);
-            if (nin > 1) col(i1, kf * f0 * f2);
-            if (nin > 2) col(i2, kf * f0 * f1);
-            if (ENERGY) col(ns, static_cast<float>(k * (t.b[r] + t.th[r] * invT) * invT * p01 * y2));
+#pragma unroll
+        for (int q = 0; q < kChunk; ++q) {
+            if (r0 + q >= nr) break;
+            const int r = r0 + q;
+            const unsigned long long ix = ixq[q];
+            const int nin = S2 ? 2 : static_cast<int>(ix & 0xff);
+            const int nout = S2 ? 2 : static_cast<int>((ix >> 8) & 0xff);
+            const int i0 = static_cast<int>((ix >> 16) & 0xff), i1 = static_cast<int>((ix >> 24) & 0xff),
+                      i2 = static_cast<int>((ix >> 32) & 0xff);
+            const int o0 = static_cast<int>((ix >> 40) & 0xff), o1 = static_cast<int>((ix >> 48) & 0xff),
+                      o2 = static_cast<int>((ix >> 56) & 0xff);
+            const double k = kq[q], y0 = y0q[q], y1 = y1q[q], y2 = y2q[q], w = wq[q];
+            wadd(i0, -w);
+            if (nin > 1) wadd(i1, -w);
+            if (!S2 && nin > 2) wadd(i2, -w);
+            if (nout > 0) wadd(o0, w);
+            if (nout > 1) wadd(o1, w);
+            if (!S2 && nout > 2) wadd(o2, w);
+            double dHr = 0.0;
+            if (ENERGY) {
+                dHr = t.dH[r];
+                fT -= dHr * w;
+            }
+            if (MODE == 1) {
+                // M = I - h J: a reactant row gains +h dw/dy_m, a product row -h dw/dy_m,
+                // the T row +h (dH_r/C_V) dw/dy_m.
+                const double hk = hph * k;
+                const double q2 = ENERGY ? dHr * invCV : 0.0;
+                auto col = [&](int m, double hd) {
+                    LI(M64, i0 * N + m) += hd;
+                    if (nin > 1) LI(M64, i1 * N + m) += hd;
+                    if (!S2 && nin > 2) LI(M64, i2 * N + m) += hd;
+                    if (nout > 0) LI(M64, o0 * N + m) -= hd;
+                    if (nout > 1) LI(M64, o1 * N + m) -= hd;
+                    if (!S2 && nout > 2) LI(M64, o2 * N + m) -= hd;
+                    if (ENERGY) LI(M64, ns * N + m) += q2 * hd;
+                };
+                col(i0, S2 ? hk * y1 : hk * y1 * y2);
+                if (nin > 1) col(i1, S2 ? hk * y0 : hk * y0 * y2);
+                if (!S2 && nin > 2) col(i2, hk * (y0 * y1));
+                if (ENERGY) {
+                    const double dkh = hph * (k * (t.b[r] + t.th[r] * invT) * invT);
+                    col(ns, S2 ? dkh * (y0 * y1) : dkh * (y0 * y1) * y2);
+                }
+            }
+            if (MODE == 2 && doJ) {
+                const float kf = static_cast<float>(k);
+                const float f0 = static_cast<float>(y0), f1 = static_cast<float>(y1),
+                            f2 = static_cast<float>(y2);
+                const float qf = ENERGY ? static_cast<float>(dHr * invCV) : 0.0f;
+                auto col = [&](int m, float d) {
+                    LIS(J32, i0 * N + m, 6) -= d;
+                    if (nin > 1) LIS(J32, i1 * N + m, 6) -= d;
+                    if (!S2 && nin > 2) LIS(J32, i2 * N + m, 6) -= d;
+                    if (nout > 0) LIS(J32, o0 * N + m, 6) += d;
+                    if (nout > 1) LIS(J32, o1 * N + m, 6) += d;
+                    if (!S2 && nout > 2) LIS(J32, o2 * N + m, 6) += d;
+                    if (ENERGY) LIS(J32, ns * N + m, 6) -= qf * d;
+                };
+                col(i0, S2 ? kf * f1 : kf * f1 * f2);
+                if (nin > 1) col(i1, S2 ? kf * f0 : kf * f0 * f2);
+                if (!S2 && nin > 2) col(i2, kf * f0 * f1);
+                if (ENERGY) {
+                    const double dw = k * (t.b[r] + t.th[r] * invT) * invT * (y0 * y1);
+                    col(ns, static_cast<float>(S2 ? dw : dw * y2));
+                }
+            }
         }
     }
     if (ENERGY) LI(W, ns) = fT * invCV;
@@ -276,7 +325,7 @@ __device__ __forceinline__ void crout_solve(const T *M, const T *V, const int *P
 }
 
 template <int NT, bool ENERGY, bool F32, bool PERSIST, bool MLPG>
-__global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a, const LaneLayout L)
+__global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArgs a, const LaneLayout L)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     const NetView nv = a.nv;
@@ -298,6 +347,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
     double *YH = reinterpret_cast<double *>(wb + L.off_YH) + lane;
     double *Y2 = reinterpret_cast<double *>(wb + L.off_Y2) + lane;
     double *W = reinterpret_cast<double *>(wb + L.off_W) + lane;
+    double *FY = F32 ? reinterpret_cast<double *>(wb + L.off_FY) + lane : nullptr;
+    const bool s2 = nv.shape == 22;   // every reaction A + B -> C + D
     int *P = reinterpret_cast<int *>(wb + L.off_P) + lane;
     double *K = ENERGY ? nullptr : reinterpret_cast<double *>(wb + L.off_K) + lane;
     // FP64 matrix and scales; in the FP32 form they overlay the lane's own J32/M32 and
@@ -326,7 +377,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
     // rescue -> this solve runs full FP64 Newton from its starting guess
     bool needJ = false, needF = false, luok = true, rescue = false;
     int refresh = 0;
-    double dprev = 0.0;
+    float dprev = 0.0f, dprevr = 0.0f;
+    // FP32 form caches: atY -> the current solve's iterate is the attempt's start
+    // state Y (bit for bit); fyok -> FY holds f(Y); jY -> J32 holds J(Y).  Phase 1
+    // starts from Y like phase 0, and a rejected attempt restarts from the same Y, so
+    // these passes reuse f(Y) (and J(Y)) instead of recomputing them.
+    bool atY = false, fyok = false, jY = false;
     // learned guess: needG -> the attempt's first solve wants the MLP's starting point;
     // usedG -> the current solve started from it (fall back to the plain start on failure)
     bool needG = false, usedG = false;
@@ -336,6 +392,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
 
     // Pre-processing (Sec. 2.2.2): floors y >= 0 and T clamped to [t_min, t_max].
     auto load_pre = [&]() {
+        fyok = false;
+        jY = false;
         for (int s = 0; s < ns; ++s) {
             const double v = a.y_in[static_cast<long long>(s) * nc + cell];
             LI(Y, s) = v > 0.0 ? v : 0.0;
@@ -365,6 +423,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
         phase = 0;
         it = 0;
         for (int i = 0; i < N; ++i) LI(YF, i) = LI(Y, i);
+        atY = true;
         if (F32) {
             needJ = true;
             needF = true;
@@ -489,7 +548,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
         invCV = ENERGY ? 1.0 / cvt : 0.0;
         atol_s = (o.atol_mode == 1 && b00 > 0.0) ? o.atol * b00 : o.atol;
         if (!ENERGY) {
-            const double lt = log(T_iso / nv.t_ref), invT = 1.0 / T_iso;
+            const double lt = log_t(T_iso, nv.t_ref), invT = 1.0 / T_iso;
             for (int r = 0; r < nr; ++r) {
                 double k, dk;
                 arrhenius(t, r, lt, invT, k, dk);
@@ -512,6 +571,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
         double *yt = phase == 0 ? YF : (phase == 1 ? YH : Y2);
         const double *g = phase == 2 ? (o.guess != KT_GUESS_PREV ? YF : YH) : Y;
         for (int i = 0; i < N; ++i) LI(yt, i) = LI(g, i);
+        atY = phase != 2;
         it = 0;
     };
 
@@ -549,6 +609,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
         const double err = sqrt(s2 / N);
         if (err <= 1.0) {
             for (int i = 0; i < N; ++i) LI(Y, i) = LI(Y2, i);
+            fyok = false;
+            jY = false;
             ++nacc;
             if (last) {
                 if (post_process()) {
@@ -585,12 +647,14 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
             phase = 1;
             it = 0;
             for (int i = 0; i < N; ++i) LI(YH, i) = LI(Y, i);
+            atY = true;
             if (F32) { needF = true; }
         } else if (phase == 1) {
             phase = 2;
             it = 0;
             const double *g2 = o.guess != KT_GUESS_PREV ? YF : YH;
             for (int i = 0; i < N; ++i) LI(Y2, i) = LI(g2, i);
+            atY = false;
         } else {
             step_done();
         }
@@ -609,9 +673,13 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
                 if (lane == leader) base = atomicAdd(&a.scratch->queue, static_cast<unsigned long long>(__popc(m)));
                 base = __shfl_sync(kFull, base, leader);
                 if (want) {
-                    cell = static_cast<long long>(base + __popc(m & ((1u << lane) - 1u)));
-                    if (cell >= nc) state = kDone;
-                    else begin_cell();
+                    const long long q = static_cast<long long>(base + __popc(m & ((1u << lane) - 1u)));
+                    if (q >= nc) {
+                        state = kDone;
+                    } else {
+                        cell = a.order ? static_cast<long long>(a.order[q]) : q;
+                        begin_cell();
+                    }
                 }
             } else {
                 if (!__any_sync(kFull, want)) break;
@@ -661,6 +729,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
                     }
                     needG = false;
                     usedG = true;
+                    atY = false;
                 }
             }
         }
@@ -676,17 +745,33 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
         double lt = 0.0, invT = 0.0;
         if (ENERGY) {
             const double Ts = bad ? 1.0 : T;
-            lt = log(Ts / nv.t_ref);
+            lt = log_t(Ts, nv.t_ref);
             invT = 1.0 / Ts;
         }
         if (!F32 || rescue) {
-            reaction_pass<NT, ENERGY, 1>(nv, t, yt, K, lt, invT, invCV, hph, W, M64, nullptr, false);
+            if (s2)
+                reaction_pass<NT, ENERGY, 1, true>(nv, t, yt, K, lt, invT, invCV, hph, W, M64, nullptr, false);
+            else
+                reaction_pass<NT, ENERGY, 1, false>(nv, t, yt, K, lt, invT, invCV, hph, W, M64, nullptr, false);
+            if (F32) jY = false;   // the FP64 matrix overlays the FP32 Jacobian
             for (int i = 0; i < N; ++i) LI(W, i) = -(LI(yt, i) - LI(yb, i) - hph * LI(W, i));
             luok = crout_lu<double, 5>(M64, V64, P, N);
             crout_solve<double, 5>(M64, V64, P, W, N);
         } else {
-            const bool doJ = needJ;
-            reaction_pass<NT, ENERGY, 2>(nv, t, yt, K, lt, invT, invCV, hph, W, nullptr, J32, doJ);
+            const bool doJ = needJ && !(atY && jY);
+            if (atY && fyok && !doJ) {
+                for (int i = 0; i < N; ++i) LI(W, i) = LI(FY, i);
+            } else {
+                if (s2)
+                    reaction_pass<NT, ENERGY, 2, true>(nv, t, yt, K, lt, invT, invCV, hph, W, nullptr, J32, doJ);
+                else
+                    reaction_pass<NT, ENERGY, 2, false>(nv, t, yt, K, lt, invT, invCV, hph, W, nullptr, J32, doJ);
+                if (atY) {
+                    for (int i = 0; i < N; ++i) LI(FY, i) = LI(W, i);
+                    fyok = true;
+                }
+                if (doJ) jY = atY;
+            }
             if (needF) {
                 for (int i = 0; i < N; ++i)
                     for (int j = 0; j < N; ++j)
@@ -702,17 +787,35 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
             for (int i = 0; i < N; ++i) LI(W, i) = static_cast<double>(LIS(X32, i, 6));
         }
         bool conv = !bad && luok;
-        double dmax = 0.0;
+        // contraction monitors of the FP32 form (FP32 is plenty): dmax = max |delta|/tol,
+        // dmaxr = max |delta| / (newton_rtol |y|), the purely relative part
+        float dmax = 0.0f, dmaxr = 0.0f;
+        const double natol = natol_frac * atol_s;
+        const float natol_f = static_cast<float>(natol);
         for (int i = 0; i < N; ++i) {
             const double d = LI(W, i);
             const double y = LI(yt, i) + d;
             LI(yt, i) = y;
-            const double tol = (i < ns ? natol_frac * atol_s : 0.0) + o.newton_rtol * fabs(y);
+            const double tol = (i < ns ? natol : 0.0) + o.newton_rtol * fabs(y);
             if (!(fabs(d) <= tol)) conv = false;
             if (F32) {
-                const double q = fabs(d) / tol;
+                const float ad = static_cast<float>(fabs(d)), tf = static_cast<float>(tol);
+                const float q = __fdiv_rn(ad, fmaxf(tf, 1e-37f));
+                const float qr = __fdiv_rn(ad, fmaxf(i < ns ? tf - natol_f : tf, 1e-37f));
                 dmax = q > dmax ? q : dmax;
+                dmaxr = qr > dmaxr ? qr : dmaxr;
             }
+        }
+        atY = false;
+        // FP32 form: stop on the contraction rate (Hairer & Wanner, Solving ODEs II,
+        // Sec. IV.8): with theta = dmaxr / dprevr < 1/2 the error left after this update
+        // is about theta / (1 - theta) * |delta|; accept when that is within
+        // newton_rtol |y_i| for every component, one iteration before |delta| itself
+        // is.  Only the relative part of the tolerance is used, so species below the
+        // absolute tolerance still end as close to the root as the plain test leaves them.
+        if (F32 && !rescue && !conv && !bad && luok && it > 0) {
+            const float th = dmaxr / dprevr;
+            if (th < 0.5f && th / (1.0f - th) * dmaxr <= 1.0f) conv = true;
         }
 
         // ---- control
@@ -724,7 +827,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
         } else {
             // simplified Newton: refresh J (at the current iterate) when the
             // contraction stalls or the iteration budget of this factor is spent
-            const bool stalled = it > 0 && !(dmax < 0.5 * dprev);
+            const bool stalled = it > 0 && !(dmax < 0.5f * dprev);
             if (bad || !luok || !isfinite(dmax)) {
                 newton_fail();
             } else if (stalled || it + 1 >= o.max_newton) {
@@ -740,6 +843,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) lane_kernel(const LaunchArgs a
                 ++it;
             }
             dprev = dmax;
+            dprevr = dmaxr;
         }
     }
 }

@@ -46,11 +46,25 @@ __device__ __forceinline__ double wsum(double v)
 
 __device__ __forceinline__ bool wall(bool p) { return __all_sync(kFull, p) != 0; }
 
+// x < -700 decided on the bit pattern (integer compare; same result as the FP64 compare
+// for every non-NaN x): negative and |x| > 700.0 (0x4085E00000000000).
+__device__ __forceinline__ bool below_m700(double x)
+{
+    const long long b = __double_as_longlong(x);
+    return b < 0 && (b & 0x7fffffffffffffffLL) > 0x4085E00000000000LL;
+}
+
+// log(T / T_ref), skipping the division when T_ref is 1 (the same value bit for bit).
+__device__ __forceinline__ double log_t(double T, double t_ref)
+{
+    return log(t_ref == 1.0 ? T : T / t_ref);
+}
+
 __device__ __forceinline__ void arrhenius(const NetS &t, int r, double lt, double invT, double &k, double &dk)
 {
     const double b = t.b[r], th = t.th[r];
     const double arg = b * lt - th * invT;
-    if (arg < -700.0) {
+    if (below_m700(arg)) {
         k = 0.0;
         dk = 0.0;
     } else {
@@ -305,7 +319,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) warp_kernel(const LaunchArgs a
 
     auto coefficients = [&](double T) {
         if (ENERGY) {
-            const double lt = log(T / nv.t_ref), invT = 1.0 / T;
+            const double lt = log_t(T, nv.t_ref), invT = 1.0 / T;
             for (int r = lane; r < nr; r += 32) {
                 double k, dk;
                 arrhenius(t, r, lt, invT, k, dk);
@@ -326,7 +340,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) warp_kernel(const LaunchArgs a
     auto be_solve = [&](const double *yb, double *yt, double hph, int fmode) -> bool {
         int refresh = 0;
         bool doJ = F32 && fmode == 2, doF = F32 && fmode >= 1;
-        double dprev = 0.0;
+        float dprev = 0.0f, dprevr = 0.0f;
         for (int it = 0;; ++it) {
             ++nnew;
             const double T = ENERGY ? yt[ns] : T_iso;
@@ -366,17 +380,26 @@ __global__ void __launch_bounds__(kMaxWarps * 32) warp_kernel(const LaunchArgs a
                 for (int q = 0; q < kQ; ++q) x[q] = static_cast<double>(xf[q]);
             }
             bool conv = true;
-            double dmax = 0.0;
+            // contraction monitors (FP32 is plenty): dmax = max |delta|/tol, dmaxr =
+            // max |delta| / (newton_rtol |y|), the purely relative part of the tolerance
+            float dmax = 0.0f, dmaxr = 0.0f;
+            const double natol = o.newton_atol_frac * atol_s;
+            const float natol_f = static_cast<float>(natol);
 #pragma unroll
             for (int q = 0; q < kQ; ++q) {
                 const int i = lane + 32 * q;
                 if (i < N) {
                     const double y = yt[i] + x[q];
                     yt[i] = y;
-                    const double tol = (i < ns ? o.newton_atol_frac * atol_s : 0.0) + o.newton_rtol * fabs(y);
+                    const double tol = (i < ns ? natol : 0.0) + o.newton_rtol * fabs(y);
                     if (!(fabs(x[q]) <= tol)) conv = false;
-                    const double r = fabs(x[q]) / tol;
-                    dmax = r > dmax ? r : dmax;
+                    if (F32) {
+                        const float ad = static_cast<float>(fabs(x[q])), tf = static_cast<float>(tol);
+                        const float r = __fdiv_rn(ad, fmaxf(tf, 1e-37f));
+                        const float rr = __fdiv_rn(ad, fmaxf(i < ns ? tf - natol_f : tf, 1e-37f));
+                        dmax = r > dmax ? r : dmax;
+                        dmaxr = rr > dmaxr ? rr : dmaxr;
+                    }
                 }
             }
             __syncwarp();
@@ -385,10 +408,23 @@ __global__ void __launch_bounds__(kMaxWarps * 32) warp_kernel(const LaunchArgs a
             if (!F32) {
                 if (it + 1 >= o.max_newton) return false;
             } else {
-                for (int off = 16; off > 0; off >>= 1) dmax = fmax(dmax, __shfl_xor_sync(kFull, dmax, off));
+                for (int off = 16; off > 0; off >>= 1) {
+                    dmax = fmaxf(dmax, __shfl_xor_sync(kFull, dmax, off));
+                    dmaxr = fmaxf(dmaxr, __shfl_xor_sync(kFull, dmaxr, off));
+                }
                 dmax = __shfl_sync(kFull, dmax, 0);
+                dmaxr = __shfl_sync(kFull, dmaxr, 0);
                 if (!isfinite(dmax)) return false;
-                const bool stalled = it > 0 && !(dmax < 0.5 * dprev);
+                // stop on the contraction rate (Hairer & Wanner, Solving ODEs II, Sec. IV.8):
+                // with theta = dmaxr / dprevr < 1/2 the error left after this update is about
+                // theta / (1 - theta) * |delta|; accept when that is within newton_rtol |y_i|
+                // for every component (the relative part only: species below the absolute
+                // tolerance end as close to the root as the plain test leaves them)
+                if (it > 0) {
+                    const float th = dmaxr / dprevr;
+                    if (th < 0.5f && th / (1.0f - th) * dmaxr <= 1.0f) return true;
+                }
+                const bool stalled = it > 0 && !(dmax < 0.5f * dprev);
                 if (stalled || it + 1 >= o.max_newton) {
                     if (refresh >= 2) return false;
                     ++refresh;
@@ -397,6 +433,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) warp_kernel(const LaunchArgs a
                     it = -1;
                 }
                 dprev = dmax;
+                dprevr = dmaxr;
             }
         }
     };
@@ -560,7 +597,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) warp_kernel(const LaunchArgs a
         invCV = ENERGY ? 1.0 / cvt : 0.0;
         atol_s = (o.atol_mode == 1 && b00 > 0.0) ? o.atol * b00 : o.atol;
         if (!ENERGY) {
-            const double lt = log(T_iso / nv.t_ref), invT = 1.0 / T_iso;
+            const double lt = log_t(T_iso, nv.t_ref), invT = 1.0 / T_iso;
             for (int r = lane; r < nr; r += 32) {
                 double k, dk;
                 arrhenius(t, r, lt, invT, k, dk);
@@ -592,7 +629,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) warp_kernel(const LaunchArgs a
             if (lane == 0) c = atomicAdd(&a.scratch->queue, 1ULL);
             c = __shfl_sync(kFull, c, 0);
             if (c >= static_cast<unsigned long long>(nc)) break;
-            cell = static_cast<long long>(c);
+            cell = a.order ? static_cast<long long>(a.order[c]) : static_cast<long long>(c);
             process_cell();
         }
     } else {

@@ -183,3 +183,45 @@ def evaluate(net: kt.Network, wl: I.Workload, mlp: Optional[kt.Mlp], n_cells: in
         res[name] = dict(ms=a.elapsed_time(b), y=r["y"].cpu().numpy(), status=r["status"].cpu().numpy(),
                          nsub=r["nsub"].cpu().numpy(), nnewton=r["nnewton"].cpu().numpy())
     return dict(results=res, y0=y0.cpu().numpy(), T=T.cpu().numpy(), dt=dt.cpu().numpy())
+
+
+def study(n_pairs: int, n_cells: int, epochs: int, seed: int = 2504, log=print) -> Dict[str, object]:
+    """The learned-guess study on the Robertson workload: train on solver-generated
+    pairs, then integrate fresh test cells over per-cell dt in every (form, guess)
+    combination and report Newton iterations, time and the largest relative change of
+    the answer that the guess causes (the solver's converged result is the judge)."""
+    import torch
+    wl = I.workload(4, 1)
+    net = kt.Network(wl.network)
+    st = train(net, wl, n_pairs=n_pairs, epochs=epochs, seed=seed, log=log)
+    out = {"workload": f"Robertson ({wl.network.ns} species), {n_cells} test cells, dt log-uniform "
+                       f"1e-8..1e-5 s per cell, rtol={wl.tol.rtol:g}, atol={wl.tol.atol:g}",
+           "pairs": st["pairs"], "train_steps": st["steps"], "val_loss": st["val_loss"],
+           "seconds_data": st["seconds_data"], "seconds_train": st["seconds_train"],
+           "guess_rel_err_median": st["guess_rel_err_median"],
+           "plain_rel_err_median": st["plain_rel_err_median"], "forms": {}}
+    for form in (kt.KT_FORM_FP64, kt.KT_FORM_FP32LU):
+        ev = evaluate(net, wl, st["mlp"], n_cells, seed + 1, form=form)
+        p, m = ev["results"]["plain"], ev["results"]["mlp"]
+        big = p["y"] > 1e-20
+        rel = np.abs(m["y"] - p["y"])[big] / p["y"][big]
+        out["forms"]["fp64" if form == 0 else "fp32lu"] = {
+            "newton_plain": int(p["nnewton"].sum()), "newton_mlp": int(m["nnewton"].sum()),
+            "newton_saved_frac": float(1.0 - m["nnewton"].sum() / p["nnewton"].sum()),
+            "ms_plain": p["ms"], "ms_mlp": m["ms"],
+            "cells_per_s_plain": n_cells / (p["ms"] * 1e-3), "cells_per_s_mlp": n_cells / (m["ms"] * 1e-3),
+            "status_ok_plain": int((p["status"] == 0).sum()), "status_ok_mlp": int((m["status"] == 0).sum()),
+            "max_rel_change_of_answer": float(rel.max(initial=0.0))}
+    torch.cuda.synchronize()
+    return out
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description=study.__doc__)
+    ap.add_argument("--pairs", type=int, default=10_000_000)
+    ap.add_argument("--cells", type=int, default=262_144)
+    ap.add_argument("--epochs", type=int, default=2)
+    a = ap.parse_args()
+    print(json.dumps(study(a.pairs, a.cells, a.epochs, log=lambda *x: None)), flush=True)

@@ -44,7 +44,7 @@ class Options(ctypes.Structure):
                 ("retry", ctypes.c_int), ("atol_mode", ctypes.c_int),
                 ("block_warps", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("cells_per_warp", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("schedule", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 def lib():

@@ -107,3 +107,34 @@ def test_table_exp_against_cuda_and_libm(kt):
     ulp = np.spacing(host)
     assert np.max(np.abs(tang - host) / ulp) <= 2.0
     assert np.max(np.abs(tang - cuda) / np.spacing(cuda)) <= 2.0
+
+
+@pytest.mark.parametrize("wid,n,dt_scale", [(2, 300, 1e-2), (3, 40, 1e-6)])
+def test_longest_first_schedule_changes_no_result(kt, wid, n, dt_scale):
+    """The longest-first queue order (from the previous call's Newton counts) only moves
+    cells between lanes: every output is bit-identical to the index-order launch, with
+    and without graph replay, on the first call (no history) and on later ones."""
+    wl = I.workload(wid, n)
+    dt = wl.tol.dt * dt_scale
+    net = kt.Network(wl.network)
+    st = kt.State(net, n)
+    for form in (0, 1):
+        ref = None
+        for graph in (0, 1):
+            for sched in (0, 1):
+                opts = kt.options(wl.tol, form=form, persistent=1, use_graph=graph, schedule=sched)
+                for rep in range(2):
+                    st.upload(wl.cells.y, wl.cells.T, wl.cells.rho)
+                    st.integrate(dt, opts)
+                    out = st.download()
+                    if ref is None:
+                        ref = out
+                        assert np.all(out["nnewton"] > 0)
+                    for k in ref:
+                        assert np.array_equal(out[k], ref[k]), (form, graph, sched, rep, k)
+        fresh = kt.State(net, n)            # no history: every count is zero
+        fresh.upload(wl.cells.y, wl.cells.T, wl.cells.rho)
+        fresh.integrate(dt, kt.options(wl.tol, form=form, persistent=1, schedule=1))
+        out = fresh.download()
+        for k in ref:
+            assert np.array_equal(out[k], ref[k]), (form, "fresh", k)
