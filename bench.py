@@ -32,6 +32,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 from paper_2504_04941_gb300 import inputs as I  # noqa: E402
+from paper_2504_04941_gb300 import shard  # noqa: E402
 
 METRIC = ("cell-integrations/s over fixed Δt at 1e-6 rel error vs FP64 oracle; "
           "plain vs chosen form")
@@ -236,7 +237,7 @@ def main():
     wl0 = I.workload(args.workload, 1)
     ncells = args.ncells or I.FULL_CELLS[args.workload]
     # weak scaling: every rank integrates its own full batch (rank-dependent seed)
-    wl = I.workload(args.workload, ncells, seed=I.SEED_BASE + args.workload + 1000 * rank)
+    wl = I.workload(args.workload, ncells, seed=shard.rank_seed(args.workload, rank))
     wl.tol.dt *= args.dt_scale
     net = kt.Network(wl.network)
     dev = torch.device("cuda", local)
@@ -318,10 +319,7 @@ def main():
             st_h = state.download()
             for k in ("status", "nsub", "nnewton"):
                 out[k].copy_(torch.from_numpy(st_h[k]))
-        if world > 1:
-            t = torch.tensor([tot_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            tot_ms = float(t.item())
+        tot_ms = shard.max_over_ranks(tot_ms, dev)
         nnew = out["nnewton"].to(torch.int64).sum().item()
         nsub = out["nsub"].to(torch.int64).sum().item()
         st = out["status"].cpu().numpy()
@@ -335,7 +333,7 @@ def main():
             # queue order comes from the previous call's Newton counts)
             "warmup_ms": warm_ms,
             "options": {k: int(v) for k, v in forms[name].items()},
-            "value": world * ncells * nsteps / (tot_ms / 1e3),
+            "value": shard.weak_throughput(ncells, world, nsteps, tot_ms / 1e3),
             "ms_per_step": per_launch_ms,
             "wall_s": wall,
             "newton_iters": int(nnew), "substeps": int(nsub),
@@ -372,12 +370,9 @@ def main():
             state.download(out=ho)
         torch.cuda.synchronize()
         e2e_s = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = shard.max_over_ranks(e2e_s, dev)
         ns = wl.network.ns
-        e2e = {"value": world * ncells * args.e2e_steps / e2e_s, "unit": UNIT, "steps": args.e2e_steps,
+        e2e = {"value": shard.weak_throughput(ncells, world, args.e2e_steps, e2e_s), "unit": UNIT, "steps": args.e2e_steps,
                "h2d_bytes_per_step": ncells * (ns + 2) * 8,
                "d2h_bytes_per_step": ncells * (ns + 1) * 8 + 3 * ncells * 4}
 
@@ -402,7 +397,10 @@ def main():
                 "dtype": "f64" if head_name == "plain" else "f64+f32",
                 "data": "synthetic", "config": config_of(args, wl, ncells),
                 "forms": results, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": args.steps, "clocks": clk, "autotune": tuned}
+                # per timed step: the integrate kernel, plus the three queue-order kernels
+                # (histogram, scan, scatter) when the longest-first schedule is on
+                "gpu_launches": args.steps * (1 + (3 if forms[head_name].get("schedule") else 0)),
+                "clocks": clk, "autotune": tuned}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
