@@ -41,6 +41,11 @@ UNIT = "cell-integrations/s"
 # (nominal 1.25 TFLOP/s); FP32: 152 x 128 FMA/clk x 2 x 2.07 GHz = 80.5 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.25
 FP32_PEAK_TFLOPS = 80.5
+# DRAM bytes (read + write) per cell of one launch of the chosen-form lane kernel on the
+# combustion10 network, from the ncu capture summarised in
+# profiles/lane_kernel_fp32lu_combustion10_65536cells_dt1e-10.md (6.945 MB for 65,536
+# cells; per-cell state lives in shared memory, so the traffic does not grow with dt)
+LANE_COMBUSTION10_DRAM_BYTES_PER_CELL = 6945024 / 65536
 
 
 # ------------------------------------------------------------------ work counts
@@ -386,8 +391,11 @@ def main():
 
     if rank == 0:
         r = head
+        traffic = (LANE_COMBUSTION10_DRAM_BYTES_PER_CELL * ncells
+                   if args.workload == 2 and head_name == "chosen" else None)
         roof = {"bound": "alu", "achieved": r["fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": r["fp64_tflops"] / FP64_PEAK_TFLOPS, "traffic": None,
+                "unit": "TFLOP/s", "frac": r["fp64_tflops"] / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "pipe": "fp64", "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz "
                                                "(nominal 1.25 TFLOP/s)",
                 "kernel": f"lane_kernel ({head_name} form)"}

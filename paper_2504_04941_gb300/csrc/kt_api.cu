@@ -46,7 +46,10 @@ int align16(int x) { return (x + 15) & ~15; }
 void kt::set_error(const char *msg) { g_err = msg; }
 
 // 2^(j/32) evaluated in long double and rounded once to double.
-double kt::exp2_table(int j) { return static_cast<double>(std::exp2(static_cast<long double>(j) / 32.0L)); }
+double kt::exp2_table(int j)
+{
+    return static_cast<double>(std::exp2(static_cast<long double>(j) / static_cast<long double>(kt::kExpTable)));
+}
 
 struct kt_network {
     std::string name;
@@ -248,7 +251,7 @@ void build_blob(kt_network *n)
     v.off_cv = o; o = align16(o + 8 * n->ns);
     v.off_cnt = o; o = align16(o + 8 * n->ns * n->ne);
     v.off_idx = o; o = align16(o + 8 * n->nr);
-    v.off_exp = o; o = align16(o + 8 * 32);
+    v.off_exp = o; o = align16(o + 8 * kt::kExpTable);
     // per-species lists of (reaction, net coefficient)
     std::vector<int> rp(n->ns + 1, 0), re;
     for (int s = 0; s < n->ns; ++s) {
@@ -280,14 +283,21 @@ void build_blob(kt_network *n)
         for (int j = 0; j < n->nin[r]; ++j) dH -= n->h[n->in[r][j]];
         put(v.off_dH, r, dH);
         unsigned char *ix = n->blob.data() + v.off_idx + 8 * r;
-        ix[0] = static_cast<unsigned char>(n->nin[r]);
+        bool distinct = true;   // no species twice among the reaction's reactants and products
+        for (int a = 0; a < n->nin[r] + n->nout[r]; ++a)
+            for (int b = a + 1; b < n->nin[r] + n->nout[r]; ++b) {
+                const int sa = a < n->nin[r] ? n->in[r][a] : n->out[r][a - n->nin[r]];
+                const int sb = b < n->nin[r] ? n->in[r][b] : n->out[r][b - n->nin[r]];
+                if (sa == sb) distinct = false;
+            }
+        ix[0] = static_cast<unsigned char>(n->nin[r] | (distinct ? kt::kIdxDistinct : 0));
         ix[1] = static_cast<unsigned char>(n->nout[r]);
         for (int j = 0; j < kt::kMaxSide; ++j) {
             ix[2 + j] = static_cast<unsigned char>(j < n->nin[r] ? n->in[r][j] : kt::kIdxNone);
             ix[5 + j] = static_cast<unsigned char>(j < n->nout[r] ? n->out[r][j] : kt::kIdxNone);
         }
     }
-    for (int j = 0; j < 32; ++j) put(v.off_exp, j, kt::exp2_table(j));
+    for (int j = 0; j < kt::kExpTable; ++j) put(v.off_exp, j, kt::exp2_table(j));
     std::memcpy(n->blob.data() + v.off_rp, rp.data(), 4 * rp.size());
     if (!re.empty()) std::memcpy(n->blob.data() + v.off_re, re.data(), 4 * re.size());
     for (int s = 0; s < n->ns; ++s) {

@@ -12,6 +12,8 @@ constexpr int kMaxSide = 3;      // reactants / products per reaction
 constexpr int kMaxElements = 8;
 constexpr int kLaneMaxN = 16;    // unknowns per cell handled by the lane-per-cell kernels
 constexpr int kIdxNone = 255;
+constexpr int kIdxDistinct = 0x80;   // flag in the reactant-count byte: all species differ
+constexpr int kExpTable = 256;       // entries 2^(j/256) of the table-driven exponential
 
 // Byte layout of the device copy of a network ("blob").  Every section starts on a
 // 16-byte boundary so the whole blob can be staged into shared memory by one bulk
@@ -20,8 +22,8 @@ struct NetView {
     int ns, ne, nr, energy, N;
     int off_A, off_b, off_th, off_dH;     // double[nr]: prefactor, exponent, activation T, heat
     int off_h, off_cv, off_cnt;           // double[ns], double[ns], double[ns*ne]
-    int off_idx;                          // uint8[nr*8]: nin, nout, in0..2, out0..2
-    int off_exp;                          // double[32]: 2^(j/32) for the table-driven exp
+    int off_idx;                          // uint8[nr*8]: nin (| kIdxDistinct), nout, in0..2, out0..2
+    int off_exp;                          // double[kExpTable]: 2^(j/256) for the table-driven exp
     int off_rp, off_re, nent;             // per-species reaction lists (CSR): int32 row
                                           // pointers [ns+1]; entries (r << 8) | (nu & 0xff),
                                           // nu = net stoichiometric coefficient (nonzero)
@@ -42,7 +44,7 @@ struct DevOpts {
 struct Scratch {
     unsigned long long queue;   // next cell of the persistent work queue
     int error;                  // KT_E* recorded by a kernel (0 = none)
-    int pad;
+    unsigned rescues;           // diagnostic: FP32-LU solves redone in FP64 during the call
 };
 
 enum DevError : int { kDevErrNone = 0, kDevErrTma = 1 };

@@ -114,6 +114,41 @@ __device__ __forceinline__ double log_t(double T, double t_ref)
 
 constexpr int kChunk = 4;   // reactions whose rates are formed before their scatter
 
+// Jacobian scatter of one A + B -> C + D reaction with four different species: the
+// rows {i0, i1, o0, o1, T} and columns {i0, i1, T} it touches are all different
+// entries, so every entry is loaded first and stored after (one shared-memory round
+// trip per reaction instead of a chain of read-modify-writes the compiler must keep in
+// order).  Each entry receives the same single update as in the general code:
+// reactant rows + s d_c, product rows - s d_c, the T row + s (q d_c); s = +1 for
+// M = I - h J (d_c = h dw/dy_c), s = -1 for J itself.
+template <typename T, int SH, bool ENERGY>
+__device__ __forceinline__ void scatter22(T *A, int N, int ns, int i0, int i1, int o0, int o1, T d0, T d1,
+                                          T d2, T q, T s)
+{
+    constexpr int NR = ENERGY ? 5 : 4, NC = ENERGY ? 3 : 2;
+    const int rows[5] = {i0, i1, o0, o1, ns};
+    const int cols[3] = {i0, i1, ns};
+    const T dc[3] = {d0, d1, d2};
+    T v[NR][NC];
+#pragma unroll
+    for (int a = 0; a < NR; ++a)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) v[a][c] = LIS(A, rows[a] * N + cols[c], SH);
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const T sd = s * dc[c];
+        v[0][c] += sd;
+        v[1][c] += sd;
+        v[2][c] -= sd;
+        v[3][c] -= sd;
+        if (ENERGY) v[4][c] = fma(s * q, dc[c], v[4][c]);
+    }
+#pragma unroll
+    for (int a = 0; a < NR; ++a)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) LIS(A, rows[a] * N + cols[c], SH) = v[a][c];
+}
+
 // One pass over the reactions at state yt (Eq. method-ode-thermochem and the
 // mass-action / thermal-coupling partials of Eq. method-jacobian):
 //   W  <- f(yt)                                   (always, FP64)
@@ -136,7 +171,6 @@ __device__ __forceinline__ void reaction_pass(const NetView &nv, const NetSmem &
     const int N = NT > 0 ? NT : nv.N, ns = nv.ns, nr = nv.nr;
 #pragma unroll
     for (int i = 0; i < N; ++i) LI(W, i) = 0.0;
-    auto wadd = [&](int i, double v) { LI(W, i) += v; };
     if (MODE == 1) {
         for (int e = 0; e < N * N; ++e) LI(M64, e) = 0.0;
     }
@@ -152,7 +186,7 @@ __device__ __forceinline__ void reaction_pass(const NetView &nv, const NetSmem &
             const int r = r0 + q < nr ? r0 + q : nr - 1;
             const unsigned long long ix = t.idx[r];
             ixq[q] = ix;
-            const int nin = S2 ? 2 : static_cast<int>(ix & 0xff);
+            const int nin = S2 ? 2 : static_cast<int>(ix & 0x7f);
             const int i0 = static_cast<int>((ix >> 16) & 0xff), i1 = static_cast<int>((ix >> 24) & 0xff),
                       i2 = static_cast<int>((ix >> 32) & 0xff);
             const double k = ENERGY ? arrhenius_k(t, r, lt, invT) : LI(K, r);
@@ -170,25 +204,41 @@ __device__ __forceinline__ void reaction_pass(const NetView &nv, const NetSmem &
             if (r0 + q >= nr) break;
             const int r = r0 + q;
             const unsigned long long ix = ixq[q];
-            const int nin = S2 ? 2 : static_cast<int>(ix & 0xff);
+            const int nin = S2 ? 2 : static_cast<int>(ix & 0x7f);
             const int nout = S2 ? 2 : static_cast<int>((ix >> 8) & 0xff);
+            const bool dist = S2 && (ix & kIdxDistinct);
             const int i0 = static_cast<int>((ix >> 16) & 0xff), i1 = static_cast<int>((ix >> 24) & 0xff),
                       i2 = static_cast<int>((ix >> 32) & 0xff);
             const int o0 = static_cast<int>((ix >> 40) & 0xff), o1 = static_cast<int>((ix >> 48) & 0xff),
                       o2 = static_cast<int>((ix >> 56) & 0xff);
             const double k = kq[q], y0 = y0q[q], y1 = y1q[q], y2 = y2q[q], w = wq[q];
-            wadd(i0, -w);
-            if (nin > 1) wadd(i1, -w);
-            if (!S2 && nin > 2) wadd(i2, -w);
-            if (nout > 0) wadd(o0, w);
-            if (nout > 1) wadd(o1, w);
-            if (!S2 && nout > 2) wadd(o2, w);
+            if (dist) {
+                // four different species: load the four entries, then store them (one
+                // shared-memory round trip instead of a chain of read-modify-writes)
+                const double a0 = LI(W, i0), a1 = LI(W, i1), b0 = LI(W, o0), b1 = LI(W, o1);
+                LI(W, i0) = a0 - w;
+                LI(W, i1) = a1 - w;
+                LI(W, o0) = b0 + w;
+                LI(W, o1) = b1 + w;
+            } else {
+                LI(W, i0) -= w;
+                if (nin > 1) LI(W, i1) -= w;
+                if (!S2 && nin > 2) LI(W, i2) -= w;
+                if (nout > 0) LI(W, o0) += w;
+                if (nout > 1) LI(W, o1) += w;
+                if (!S2 && nout > 2) LI(W, o2) += w;
+            }
             double dHr = 0.0;
             if (ENERGY) {
                 dHr = t.dH[r];
                 fT -= dHr * w;
             }
-            if (MODE == 1) {
+            if (MODE == 1 && dist) {
+                const double hk = hph * k;
+                const double d2 = ENERGY ? hph * (k * (t.b[r] + t.th[r] * invT) * invT) * (y0 * y1) : 0.0;
+                scatter22<double, 5, ENERGY>(M64, N, ns, i0, i1, o0, o1, hk * y1, hk * y0, d2,
+                                             ENERGY ? dHr * invCV : 0.0, 1.0);
+            } else if (MODE == 1) {
                 // M = I - h J: a reactant row gains +h dw/dy_m, a product row -h dw/dy_m,
                 // the T row +h (dH_r/C_V) dw/dy_m.
                 const double hk = hph * k;
@@ -210,7 +260,13 @@ __device__ __forceinline__ void reaction_pass(const NetView &nv, const NetSmem &
                     col(ns, S2 ? dkh * (y0 * y1) : dkh * (y0 * y1) * y2);
                 }
             }
-            if (MODE == 2 && doJ) {
+            if (MODE == 2 && doJ && dist) {
+                const float kf = static_cast<float>(k);
+                const float f0 = static_cast<float>(y0), f1 = static_cast<float>(y1);
+                const float d2 = ENERGY ? static_cast<float>(k * (t.b[r] + t.th[r] * invT) * invT * (y0 * y1)) : 0.0f;
+                scatter22<float, 6, ENERGY>(J32, N, ns, i0, i1, o0, o1, kf * f1, kf * f0, d2,
+                                            ENERGY ? static_cast<float>(dHr * invCV) : 0.0f, -1.0f);
+            } else if (MODE == 2 && doJ) {
                 const float kf = static_cast<float>(k);
                 const float f0 = static_cast<float>(y0), f1 = static_cast<float>(y1),
                             f2 = static_cast<float>(y2);
@@ -591,6 +647,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
         }
         if (F32 && !rescue) {
             rescue = true;
+            atomicAdd(&a.scratch->rescues, 1u);
             restart_solve();
             return;
         }

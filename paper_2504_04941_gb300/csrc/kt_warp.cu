@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) warp_kernel(const LaunchArgs a
                 const int r = ent >> 8;
                 const double nu = static_cast<double>(static_cast<signed char>(ent & 0xff));
                 const unsigned long long ix = t.idx[r];
-                const int nin = static_cast<int>(ix & 0xff);
+                const int nin = static_cast<int>(ix & 0x7f);
                 const int i0 = static_cast<int>((ix >> 16) & 0xff), i1 = static_cast<int>((ix >> 24) & 0xff),
                           i2 = static_cast<int>((ix >> 32) & 0xff);
                 const double k = K[r];
