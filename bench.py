@@ -182,7 +182,8 @@ def reference_arm(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(args, wl, n),
+            # the GPU arm's workload; each step times a bounded sample of its cells
+            "config": config_of(args, wl, args.ncells or I.FULL_CELLS[args.workload]),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{n} cells of the {wl.name} workload per step (same "
                                        f"network, tolerances and dt), pthreads over cells"},

@@ -73,7 +73,10 @@ typedef struct kt_mlp kt_mlp;
  * weighted RMS of their difference with weights atol_i + rtol*max(|y_i|,|y2_i|)
  * must be <= 1; the next h is h*min(facmax, max(0.2, 0.9/sqrt(err))).  Newton on
  * each step stops when every |delta_i| <= newton_atol_frac*atol_i + newton_rtol*|y_i|
- * (temperature: newton_rtol*|T|) and fails after max_newton iterations (h halves). */
+ * (temperature: newton_rtol*|T|) and fails after max_newton iterations (h halves).
+ * The FP32-LU form also stops one iteration earlier when the contraction rate theta
+ * of its simplified Newton iteration (< 1/2) predicts that the error left,
+ * theta/(1-theta)*|delta_i|, is within newton_rtol*|y_i| for every component. */
 typedef struct {
     double rtol;             /* relative error weight                          (1e-6) */
     double atol;             /* absolute error weight of every species         (1e-10) */

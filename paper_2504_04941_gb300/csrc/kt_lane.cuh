@@ -112,7 +112,12 @@ __device__ __forceinline__ double log_t(double T, double t_ref)
     return log(t_ref == 1.0 ? T : T / t_ref);
 }
 
-constexpr int kChunk = 4;   // reactions whose rates are formed before their scatter
+// reactions whose rates are formed before their scatter (independent FP64 chains in
+// flight); a build-time tuning knob, the results do not depend on it
+#ifndef KT_LANE_CHUNK
+#define KT_LANE_CHUNK 4
+#endif
+constexpr int kChunk = KT_LANE_CHUNK;
 
 // Jacobian scatter of one A + B -> C + D reaction with four different species: the
 // rows {i0, i1, o0, o1, T} and columns {i0, i1, T} it touches are all different

@@ -194,7 +194,7 @@ __device__ void warp_solve(const T *M, const T *V, const int *G, const TB *Wb, T
 }
 
 template <bool ENERGY, bool F32, bool PERSIST>
-__global__ void __launch_bounds__(kMaxWarps * 32) warp_kernel(const LaunchArgs a, const WarpLayout L)
+__global__ void __launch_bounds__(kMaxWarps * 32, 2) warp_kernel(const LaunchArgs a, const WarpLayout L)
 {
     extern __shared__ __align__(16) unsigned char sm[];
     const NetView nv = a.nv;
@@ -277,18 +277,36 @@ __global__ void __launch_bounds__(kMaxWarps * 32) warp_kernel(const LaunchArgs a
                 const double p01 = y0 * y1;
                 f += nu * (k * p01 * y2);
                 if (wantJ) {
+                    // two different reactants: the row entries i0, i1 (and T) differ, so
+                    // they are loaded first and stored after (one shared-memory round trip
+                    // instead of a chain of read-modify-writes); same updates either way
+                    const bool two = nin == 2 && i0 != i1;
                     if (F32) {
                         float *row = J32 + s * NP;
-                        row[i0] += static_cast<float>(nu * (k * y1 * y2));
-                        if (nin > 1) row[i1] += static_cast<float>(nu * (k * y0 * y2));
-                        if (nin > 2) row[i2] += static_cast<float>(nu * (k * p01));
-                        if (ENERGY) row[ns] += static_cast<float>(nu * (DK[r] * p01 * y2));
+                        if (two) {
+                            const float a0 = row[i0], a1 = row[i1], aT = ENERGY ? row[ns] : 0.0f;
+                            row[i0] = a0 + static_cast<float>(nu * (k * y1 * y2));
+                            row[i1] = a1 + static_cast<float>(nu * (k * y0 * y2));
+                            if (ENERGY) row[ns] = aT + static_cast<float>(nu * (DK[r] * p01 * y2));
+                        } else {
+                            row[i0] += static_cast<float>(nu * (k * y1 * y2));
+                            if (nin > 1) row[i1] += static_cast<float>(nu * (k * y0 * y2));
+                            if (nin > 2) row[i2] += static_cast<float>(nu * (k * p01));
+                            if (ENERGY) row[ns] += static_cast<float>(nu * (DK[r] * p01 * y2));
+                        }
                     } else {
                         double *row = M64 + s * NP;
-                        row[i0] += nu * (k * y1 * y2);
-                        if (nin > 1) row[i1] += nu * (k * y0 * y2);
-                        if (nin > 2) row[i2] += nu * (k * p01);
-                        if (ENERGY) row[ns] += nu * (DK[r] * p01 * y2);
+                        if (two) {
+                            const double a0 = row[i0], a1 = row[i1], aT = ENERGY ? row[ns] : 0.0;
+                            row[i0] = a0 + nu * (k * y1 * y2);
+                            row[i1] = a1 + nu * (k * y0 * y2);
+                            if (ENERGY) row[ns] = aT + nu * (DK[r] * p01 * y2);
+                        } else {
+                            row[i0] += nu * (k * y1 * y2);
+                            if (nin > 1) row[i1] += nu * (k * y0 * y2);
+                            if (nin > 2) row[i2] += nu * (k * p01);
+                            if (ENERGY) row[ns] += nu * (DK[r] * p01 * y2);
+                        }
                     }
                 }
             }
