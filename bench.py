@@ -264,8 +264,8 @@ def main():
     tuned = None
     if not args.no_tune:
         base = kt.options(wl.tol, **forms["chosen"])
-        cache = os.path.join(ROOT, "gpurun_out", "tuned.json") if os.path.isdir(
-            os.path.join(ROOT, "gpurun_out")) else os.path.join(ROOT, ".tuned.json")
+        # launch-shape cache (per network size, form and GPU name)
+        cache = os.environ.get("KT_TUNE_CACHE", os.path.join(ROOT, ".tuned.json"))
         # tune the launch shape on the whole batch over a short interval (dt/1000): every
         # candidate runs at full occupancy in well under a second
         topts, tuned = kt.tuned_options(net, y_in, T_in, wl.tol.dt * 1e-3, base, cache,

@@ -189,7 +189,7 @@ def study(n_pairs: int, n_cells: int, epochs: int, seed: int = 2504, log=print) 
     """The learned-guess study on the Robertson workload: train on solver-generated
     pairs, then integrate fresh test cells over per-cell dt in every (form, guess)
     combination and report Newton iterations, time and the largest relative change of
-    the answer that the guess causes (the solver's converged result is the judge)."""
+    the answer that the guess causes (the solver's converged result decides)."""
     import torch
     wl = I.workload(4, 1)
     net = kt.Network(wl.network)
