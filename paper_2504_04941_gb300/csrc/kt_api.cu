@@ -406,6 +406,36 @@ size_t kt_scratch_bytes(void) { return sizeof(kt::Scratch); }
 
 namespace {
 
+// Longest-first order of the state's cells from the Newton counts of the previous call
+// (opts.schedule with a persistent launch); buffers are allocated on first use, outside
+// any stream capture.  *order is null when the option is off.
+int state_schedule(kt_state *st, const kt_options *opts, cudaStream_t s, bool launch, const int **order)
+{
+    *order = nullptr;
+    if (!opts->schedule || !opts->persistent || st->ncells > 0x7fffffffLL) return KT_OK;
+    if (!st->order || !st->sched_work) {
+        cudaFree(st->order);
+        cudaFree(st->sched_work);
+        st->order = nullptr;
+        st->sched_work = nullptr;
+        cudaError_t e = cudaMalloc(&st->order, static_cast<size_t>(st->ncells) * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc(&st->sched_work, 2 * kt::kSchedBuckets * sizeof(unsigned));
+        if (e != cudaSuccess) {
+            cudaFree(st->order);
+            cudaFree(st->sched_work);
+            st->order = nullptr;
+            st->sched_work = nullptr;
+            return fail(KT_ENOMEM, "kt_integrate: schedule buffers: %s", cudaGetErrorString(e));
+        }
+    }
+    if (launch) {
+        const int ce = kt::launch_schedule(st->nnew, st->ncells, st->sched_work, st->order, s);
+        if (ce != 0) return cuda_fail(static_cast<cudaError_t>(ce), "schedule kernels");
+    }
+    *order = st->order;
+    return KT_OK;
+}
+
 int integrate_impl(const kt_network *net, int64_t ncells, const double *y_in, const double *T_in,
                    const double *rho, const double *dt_cell, double dt, const kt_options *opts, double *y_out,
                    double *T_out, int32_t *status, int32_t *n_substeps, int32_t *n_newton, void *scratch,
@@ -615,30 +645,6 @@ int kt_state_upload(kt_state *st, const double *y, const double *T, const double
     if (e != cudaSuccess) return cuda_fail(e, "kt_state_upload");
     return KT_OK;
 }
-
-namespace {
-
-// Longest-first order of the state's cells from the Newton counts of the previous call
-// (opts.schedule with a persistent launch); buffers are allocated on first use, outside
-// any stream capture.  *order is null when the option is off.
-int state_schedule(kt_state *st, const kt_options *opts, cudaStream_t s, bool launch, const int **order)
-{
-    *order = nullptr;
-    if (!opts->schedule || !opts->persistent || st->ncells > 0x7fffffffLL) return KT_OK;
-    if (!st->order) {
-        cudaError_t e = cudaMalloc(&st->order, static_cast<size_t>(st->ncells) * sizeof(int));
-        if (e == cudaSuccess) e = cudaMalloc(&st->sched_work, 2 * kt::kSchedBuckets * sizeof(unsigned));
-        if (e != cudaSuccess) return fail(KT_ENOMEM, "kt_integrate: schedule buffers: %s", cudaGetErrorString(e));
-    }
-    if (launch) {
-        const int ce = kt::launch_schedule(st->nnew, st->ncells, st->sched_work, st->order, s);
-        if (ce != 0) return cuda_fail(static_cast<cudaError_t>(ce), "schedule kernels");
-    }
-    *order = st->order;
-    return KT_OK;
-}
-
-}  // namespace
 
 int kt_integrate(kt_state *st, double dt, const kt_options *opts, void *cuda_stream)
 {
