@@ -639,8 +639,10 @@ int kt_state_upload(kt_state *st, const double *y, const double *T, const double
     if (e == cudaSuccess) e = cudaMemcpyAsync(st->T, T, n * sizeof(double), k, s);
     if (e == cudaSuccess && rho) e = cudaMemcpyAsync(st->rho, rho, n * sizeof(double), k, s);
     if (e == cudaSuccess && !rho) {
+        // ordered on the caller's stream; a pageable source is staged before the call
+        // returns, so the local vector may go out of scope
         std::vector<double> ones(n, 1.0);
-        e = cudaMemcpy(st->rho, ones.data(), n * sizeof(double), cudaMemcpyHostToDevice);
+        e = cudaMemcpyAsync(st->rho, ones.data(), n * sizeof(double), cudaMemcpyHostToDevice, s);
     }
     if (e != cudaSuccess) return cuda_fail(e, "kt_state_upload");
     return KT_OK;

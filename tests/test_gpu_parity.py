@@ -190,3 +190,20 @@ def test_state_api_host_roundtrip(kt):
     d = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, opts, net)
     for k in ("y", "T", "status", "nsub", "nnewton"):
         assert np.array_equal(h[k], d[k]), k
+
+
+def test_state_upload_without_density(kt):
+    """A state uploaded without densities (rho = 1 filled by the library on the caller's
+    stream) integrates exactly like the device-buffer call with no density."""
+    import torch
+    wl = I.workload(2, 64)
+    net = kt.Network(wl.network)
+    opts = kt.options(wl.tol, form=1, persistent=1)
+    st = kt.State(net, 64)
+    stream = torch.cuda.Stream()
+    st.upload(wl.cells.y, wl.cells.T, None, stream=stream)
+    st.integrate(wl.tol.dt * 1e-3, opts, stream=stream)
+    h = st.download(stream=stream)
+    d = gpu_run(kt, wl.network, wl.cells, wl.tol.dt * 1e-3, opts, net)
+    for k in ("y", "T", "status", "nsub", "nnewton"):
+        assert np.array_equal(h[k], d[k]), k
