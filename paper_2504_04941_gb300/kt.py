@@ -157,6 +157,56 @@ def _ptr(t) -> Optional[int]:
     return None if t is None else t.data_ptr()
 
 
+# The C ABI sees raw pointers and sizes only, so every buffer is checked here before a
+# pointer is passed on: a wrong shape, dtype or device would make a kernel or a host copy
+# run past the end of the caller's memory.
+
+def _require(t, name: str, shape, dtype: str, optional: bool = False):
+    """Raise ValueError unless t is a contiguous CUDA tensor of that shape and dtype
+    (``dtype`` names a torch dtype, e.g. "float64"); None passes when optional."""
+    if t is None:
+        if optional:
+            return
+        raise ValueError(f"{name} is required")
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if str(t.dtype) != f"torch.{dtype}" or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous {dtype} tensor of shape {tuple(shape)}; "
+                         f"got {t.dtype} {tuple(t.shape)}")
+
+
+def _require_host(a, name: str, shape, dtype, optional: bool = False):
+    """Raise ValueError unless a is a C-contiguous numpy array of that shape and dtype."""
+    if a is None:
+        if optional:
+            return
+        raise ValueError(f"{name} is required")
+    if not isinstance(a, np.ndarray) or a.dtype != np.dtype(dtype) or tuple(a.shape) != tuple(shape) \
+            or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError(f"{name} must be a C-contiguous {np.dtype(dtype)} array of shape {tuple(shape)}")
+
+
+def _require_cells(net: "Network", y, T, rho=None, outs=None, scratch=None):
+    """Cell buffers of one integrate call: y [ns][ncells], T [ncells], rho [ncells] or
+    None (float64), outputs of the same shapes (int32 counters); returns ncells."""
+    if getattr(T, "dim", lambda: 0)() != 1:
+        raise ValueError("T must be a 1-D CUDA tensor of cells")
+    ncells = int(T.shape[0])
+    _require(T, "T", (ncells,), "float64")
+    _require(y, "y", (net.ns, ncells), "float64")
+    _require(rho, "rho", (ncells,), "float64", optional=True)
+    for k, v in (outs or {}).items():
+        if k in ("y", "T"):
+            _require(v, f"out[{k!r}]", (net.ns, ncells) if k == "y" else (ncells,), "float64")
+        elif k in ("status", "nsub", "nnewton"):
+            _require(v, f"out[{k!r}]", (ncells,), "int32", optional=True)
+    if scratch is not None:
+        if not getattr(scratch, "is_cuda", False) or not scratch.is_contiguous() or \
+                scratch.numel() * scratch.element_size() < scratch_bytes():
+            raise ValueError(f"scratch must be a contiguous CUDA buffer of >= {scratch_bytes()} bytes")
+    return ncells
+
+
 def _stream_handle(stream) -> Optional[int]:
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -170,7 +220,7 @@ def integrate(net: Network, y, T, dt: float, opts: Options, rho=None, out=None,
     Returns a dict of device tensors y, T, status, nsub, nnewton (``out`` may supply
     them; passing y/T themselves integrates in place).  Asynchronous on ``stream``."""
     import torch
-    ncells = T.shape[0]
+    ncells = _require_cells(net, y, T, rho, out, scratch)
     dev = T.device
     if out is None:
         out = {}
@@ -191,9 +241,7 @@ def integrate(net: Network, y, T, dt: float, opts: Options, rho=None, out=None,
         nnew = torch.empty(ncells, dtype=torch.int32, device=dev)
     if scratch is None:
         scratch = torch.empty(scratch_bytes(), dtype=torch.uint8, device=dev)
-    for tns in (y, T, yo, To):
-        if tns.dtype != torch.float64 or not tns.is_contiguous() or not tns.is_cuda:
-            raise ValueError("y, T and outputs must be contiguous float64 CUDA tensors")
+    _require_cells(net, y, T, rho, dict(y=yo, T=To, status=st, nsub=nsub, nnewton=nnew), scratch)
     _check(lib().kt_integrate_ptrs(net.ptr, ncells, _ptr(y), _ptr(T), _ptr(rho), float(dt),
                                    ctypes.byref(opts), _ptr(yo), _ptr(To), _ptr(st), _ptr(nsub),
                                    _ptr(nnew), _ptr(scratch), _stream_handle(stream)))
@@ -203,7 +251,8 @@ def integrate(net: Network, y, T, dt: float, opts: Options, rho=None, out=None,
 def integrate_dt(net: Network, y, T, dt_cells, opts: Options, out=None, scratch=None, stream=None):
     """``integrate`` with a per-cell time step (CUDA float64 tensor [ncells])."""
     import torch
-    ncells = T.shape[0]
+    ncells = _require_cells(net, y, T, None, out, scratch)
+    _require(dt_cells, "dt_cells", (ncells,), "float64")
     dev = T.device
     out = dict(out or {})
     out.setdefault("y", torch.empty_like(y))
@@ -212,9 +261,7 @@ def integrate_dt(net: Network, y, T, dt_cells, opts: Options, out=None, scratch=
         out.setdefault(k, torch.empty(ncells, dtype=torch.int32, device=dev))
     if scratch is None:
         scratch = torch.empty(scratch_bytes(), dtype=torch.uint8, device=dev)
-    for tns in (y, T, dt_cells, out["y"], out["T"]):
-        if tns.dtype != torch.float64 or not tns.is_contiguous() or not tns.is_cuda:
-            raise ValueError("y, T, dt_cells and outputs must be contiguous float64 CUDA tensors")
+    _require_cells(net, y, T, None, out, scratch)
     _check(lib().kt_integrate_dt(net.ptr, ncells, _ptr(y), _ptr(T), None, _ptr(dt_cells),
                                  ctypes.byref(opts), _ptr(out["y"]), _ptr(out["T"]),
                                  _ptr(out["status"]), _ptr(out["nsub"]), _ptr(out["nnewton"]),
@@ -252,9 +299,16 @@ class State:
     def upload(self, y, T, rho=None, stream=None):
         """y, T, rho: numpy arrays (host) or CUDA tensors (device)."""
         dev = hasattr(y, "data_ptr") and getattr(y, "is_cuda", False)
+        ns, nc = self.net.ns, self.ncells
         if dev:
+            _require(y, "y", (ns, nc), "float64")
+            _require(T, "T", (nc,), "float64")
+            _require(rho, "rho", (nc,), "float64", optional=True)
             args = (_ptr(y), _ptr(T), _ptr(rho))
         else:
+            _require_host(y, "y", (ns, nc), np.float64)
+            _require_host(T, "T", (nc,), np.float64)
+            _require_host(rho, "rho", (nc,), np.float64, optional=True)
             args = (_np_ptr(y), _np_ptr(T), _np_ptr(rho))
         _check(lib().kt_state_upload(self.ptr, *args, int(dev), _stream_handle(stream)))
 
@@ -267,6 +321,10 @@ class State:
         if out is None:
             out = dict(y=np.empty((ns, nc)), T=np.empty(nc), status=np.empty(nc, np.int32),
                        nsub=np.empty(nc, np.int32), nnewton=np.empty(nc, np.int32))
+        _require_host(out["y"], "out['y']", (ns, nc), np.float64)
+        _require_host(out["T"], "out['T']", (nc,), np.float64)
+        for k in ("status", "nsub", "nnewton"):
+            _require_host(out[k], f"out[{k!r}]", (nc,), np.int32)
         _check(lib().kt_state_download(self.ptr, _np_ptr(out["y"]), _np_ptr(out["T"]),
                                        _np_ptr(out["status"]), _np_ptr(out["nsub"]),
                                        _np_ptr(out["nnewton"]), 0, _stream_handle(stream)))
@@ -294,6 +352,7 @@ def autotune(net: Network, y, T, dt: float, base: Options, stream=None):
 
     Returns (options, seconds of the best candidate on the sample)."""
     import torch
+    _require_cells(net, y, T)
     yo, To = torch.empty_like(y), torch.empty_like(T)
     scratch = torch.empty(scratch_bytes(), dtype=torch.uint8, device=T.device)
     best = Options()
@@ -381,6 +440,8 @@ class Mlp:
         _check(lib().kt_mlp_set_norm(self.ptr, *[_fp(x) for x in arrs]))
 
     def train_step(self, X, Tg, lr: float, want_loss: bool = False, stream=None):
+        _require(X, "X", (X.shape[0], MLP_IN), "float32")
+        _require(Tg, "targets", (X.shape[0], MLP_OUT), "float32")
         loss = ctypes.c_double()
         _check(lib().kt_mlp_train_step(self.ptr, _ptr(X), _ptr(Tg), X.shape[0], float(lr),
                                        ctypes.byref(loss) if want_loss else None,
@@ -388,6 +449,8 @@ class Mlp:
         return loss.value if want_loss else None
 
     def gradients(self, X, Tg, stream=None):
+        _require(X, "X", (X.shape[0], MLP_IN), "float32")
+        _require(Tg, "targets", (X.shape[0], MLP_OUT), "float32")
         _, n = mlp_layout()
         g = np.zeros(n, np.float32)
         loss = ctypes.c_double()
@@ -397,8 +460,10 @@ class Mlp:
 
     def forward(self, X, out=None, stream=None):
         import torch
+        _require(X, "X", (X.shape[0], MLP_IN), "float32")
         if out is None:
             out = torch.empty((X.shape[0], MLP_OUT), dtype=torch.float32, device=X.device)
+        _require(out, "out", (X.shape[0], MLP_OUT), "float32")
         _check(lib().kt_mlp_forward(self.ptr, _ptr(X), _ptr(out), X.shape[0], _stream_handle(stream)))
         return out
 
@@ -428,6 +493,7 @@ def state_load_mlp(state: "State", path: str):
 def debug_exp(x, which: int, stream=None):
     """exp of a float64 CUDA tensor by CUDA's exp (0) or the library's table-driven one (1)."""
     import torch
+    _require(x, "x", tuple(x.shape), "float64")
     out = torch.empty_like(x)
     _check(lib().kt_debug_exp(_ptr(x), _ptr(out), x.numel(), int(which), _stream_handle(stream)))
     return out
@@ -440,9 +506,7 @@ def integrate_noalloc(net: Network, y, T, dt: float, opts: Options, out, rho=Non
     work-queue counter and the network tables in a fixed static device array, so the
     caller passes inputs and preallocated outputs only (``out``: dict of CUDA tensors
     y, T, status, nsub, nnewton).  Calls that overlap on the GPU race on that array."""
-    for k in ("y", "T"):
-        if out[k].dtype != y.dtype or not out[k].is_contiguous():
-            raise ValueError("outputs must be contiguous float64 CUDA tensors")
+    _require_cells(net, y, T, rho, out)
     _check(lib().kt_integrate_noalloc(net.ptr, T.shape[0], _ptr(y), _ptr(T), _ptr(rho), float(dt),
                                       ctypes.byref(opts), _ptr(out["y"]), _ptr(out["T"]),
                                       _ptr(out.get("status")), _ptr(out.get("nsub")),
