@@ -166,6 +166,41 @@ def oracle_time(wl: I.Workload, ncells: int, seed_offset: int = 0):
     return ncells / wall, threads, wall
 
 
+def oracle_on(network: I.Network, cells: I.Cells, tol: I.Tolerances):
+    """The FP64 oracle (as it stands) on these cells with all host cores; returns
+    (result dict, threads, wall seconds)."""
+    from oracle import oracle
+    net = oracle.OracleNetwork(network)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    r = net.integrate(cells, tol.dt, oracle.options(tol), threads)
+    return r, threads, time.perf_counter() - t0
+
+
+def accuracy(gpu: dict, ora: dict, network: I.Network, y0: np.ndarray) -> dict:
+    """Errors of a GPU result against the oracle's on the same cells: the largest
+    relative error per species above 1e-20 (over all cells, and over the cells whose
+    accepted sub-step count equals the oracle's: the step-doubling accept test is a
+    discontinuous function of rounding), the largest relative error of T, and the
+    largest relative change of the element totals."""
+    yg, yo = np.asarray(gpu["y"], float), np.asarray(ora["y"], float)
+    Tg, To = np.asarray(gpu["T"], float), np.asarray(ora["T"], float)
+    big = yo > 1e-20
+    rel = np.where(big, np.abs(yg - yo) / np.where(big, yo, 1.0), 0.0)
+    same = np.asarray(gpu["nsub"]) == np.asarray(ora["nsub"])
+    y0c = np.maximum(y0, 0.0)
+    b0 = network.counts.T @ y0c
+    scale = np.abs(network.counts.T) @ y0c
+    cons = np.abs(network.counts.T @ yg - b0) / np.where(scale > 0, scale, 1.0)
+    return {"cells": int(yo.shape[1]),
+            "max_rel_err_y": float(rel.max(initial=0.0)),
+            "max_rel_err_y_same_substeps": float(rel[:, same].max(initial=0.0)),
+            "cells_with_other_substep_count": int((~same).sum()),
+            "max_rel_err_T": float((np.abs(Tg - To) / np.abs(To)).max(initial=0.0)),
+            "max_conservation_err": float(cons.max(initial=0.0)),
+            "status_equal": bool(np.array_equal(np.asarray(gpu["status"]), np.asarray(ora["status"])))}
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -240,7 +275,6 @@ def main():
         dist.init_process_group("nccl")
     from paper_2504_04941_gb300 import kt
 
-    wl0 = I.workload(args.workload, 1)
     ncells = args.ncells or I.FULL_CELLS[args.workload]
     # weak scaling: every rank integrates its own full batch (rank-dependent seed)
     wl = I.workload(args.workload, ncells, seed=shard.rank_seed(args.workload, rank))
@@ -382,13 +416,27 @@ def main():
                "h2d_bytes_per_step": ncells * (ns + 2) * 8,
                "d2h_bytes_per_step": ncells * (ns + 1) * 8 + 3 * ncells * 4}
 
-    # ---- CPU baseline: the oracle on a bounded sample (rank 0, one GPU only)
+    # ---- CPU baseline: the oracle on a bounded sample of the batch (rank 0, one GPU
+    # only), and the error of each GPU form against it on the same cells (one more
+    # launch per form on the sample, after the timed region)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, threads, wall = oracle_time(wl0, args.cpu_cells)
-        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": f"first {args.cpu_cells} cells of a fresh draw of the {wl.name} "
-                         f"workload, full dt, {wall:.1f} s wall"}
+        nsample = min(args.cpu_cells, ncells)
+        sample = wl.cells.subset(range(nsample))
+        ora, threads, wall = oracle_on(wl.network, sample, wl.tol)
+        cpu = {"value": nsample / wall, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"first {nsample} cells of the benchmark batch ({wl.name}, dt={wl.tol.dt:g} s), "
+                         f"{wall:.1f} s wall"}
+        for name in results:
+            try:
+                so = kt.options(wl.tol, **forms[name])
+                r = kt.integrate(net, torch.from_numpy(sample.y).to(dev), torch.from_numpy(sample.T).to(dev),
+                                 wl.tol.dt, so, rho=torch.from_numpy(sample.rho).to(dev))
+                kt.check_scratch(r["scratch"])
+                g = {k: r[k].cpu().numpy() for k in ("y", "T", "status", "nsub")}
+                results[name]["accuracy_vs_oracle"] = accuracy(g, ora, wl.network, sample.y)
+            except Exception as ex:          # a report, never a reason to lose the line
+                results[name]["accuracy_vs_oracle"] = {"error": repr(ex)[:300]}
 
     if rank == 0:
         r = head
@@ -399,7 +447,7 @@ def main():
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "pipe": "fp64", "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz "
                                                "(nominal 1.25 TFLOP/s)",
-                "kernel": f"lane_kernel ({head_name} form)"}
+                "kernel": f"{'lane_kernel' if wl.network.n <= 16 else 'warp_kernel'} ({head_name} form)"}
         line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
