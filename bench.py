@@ -166,6 +166,16 @@ def oracle_time(wl: I.Workload, ncells: int, seed_offset: int = 0):
     return ncells / wall, threads, wall
 
 
+def hbm_peak_gbs() -> tuple:
+    """(GB/s, source) of the measured copy bandwidth of the GB300s, else the
+    earlier single measurement."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except Exception:
+        return 6800.0, "fallback (one earlier GB300 measurement)"
+
+
 def oracle_on(network: I.Network, cells: I.Cells, tol: I.Tolerances):
     """The FP64 oracle (as it stands) on these cells with all host cores; returns
     (result dict, threads, wall seconds)."""
@@ -442,11 +452,16 @@ def main():
         r = head
         traffic = (LANE_COMBUSTION10_DRAM_BYTES_PER_CELL * ncells
                    if args.workload == 2 and head_name == "chosen" else None)
+        hbm_peak, hbm_src = hbm_peak_gbs()
+        hbm_gbs = traffic / (r["ms_per_step"] * 1e-3) / 1e9 if traffic else None
         roof = {"bound": "alu", "achieved": r["fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": r["fp64_tflops"] / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
                 "pipe": "fp64", "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz "
                                                "(nominal 1.25 TFLOP/s)",
+                # the same launch against HBM: evidence that the path is not memory bound
+                "hbm_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
+                "hbm_frac": hbm_gbs / hbm_peak if hbm_gbs else None,
                 "kernel": f"{'lane_kernel' if wl.network.n <= 16 else 'warp_kernel'} ({head_name} form)"}
         line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
