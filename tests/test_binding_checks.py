@@ -27,6 +27,8 @@ class FakeCuda:
 
 @pytest.fixture(scope="module")
 def net():
+    from paper_2504_04941_gb300 import build
+    build.build()                     # host-only use of the library (network parsing)
     return kt.Network(I.network(2))
 
 
