@@ -160,8 +160,11 @@ def evaluate(net: kt.Network, wl: I.Workload, mlp: Optional[kt.Mlp], n_cells: in
              form: int = kt.KT_FORM_FP64, dt_range=(1e-8, 1e-5)):
     """Integrate fresh test cells over per-cell dt with and without the learned guess."""
     import torch
-    y0, T = trajectory_states(net, wl, max(1, n_cells // 80), 80, seed)
+    n_snap = 80
+    n_traj = max(1, -(-n_cells // n_snap))                 # enough trajectories for n_cells
+    y0, T = trajectory_states(net, wl, n_traj, n_snap, seed)
     y0, T = y0[:, :n_cells].contiguous(), T[:n_cells].contiguous()
+    assert T.shape[0] == n_cells, (T.shape, n_cells)
     g = torch.Generator(device="cpu").manual_seed(seed + 7)
     u = torch.rand(n_cells, generator=g, dtype=torch.float64)
     dt = torch.exp(math.log(dt_range[0]) + u * (math.log(dt_range[1]) - math.log(dt_range[0]))).cuda()
