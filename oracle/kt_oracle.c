@@ -84,6 +84,7 @@ typedef struct {
     int guess;      /* Newton start of the second half step: 0 its own start state;
                        2 the full step's result (same end time).  Changes only the
                        iteration count, not the root (to the Newton tolerance). */
+    int scheme;     /* 0: backward Euler with step doubling; 1: TR-BDF2 */
 } ko_options;
 
 /* ------------------------------------------------------------------ parsing */
@@ -414,7 +415,8 @@ static double eatol(const ko_cell *c, int i)
 
 /* One backward-Euler step y = yn + h f(y), solved by full Newton from the guess in y:
  * M = I - h J(y), M delta = -(y - yn - h f(y)), y += delta, until every
- * |delta_i| <= natol_i + newton_rtol |y_i|.  Returns 0 on convergence. */
+ * |delta_i| <= natol_i + newton_rtol |y_i|.  Returns 0 on convergence.  The TR-BDF2
+ * stages are equations of the same form, y = r + c f(y), with r and c given below. */
 static int be_solve(ko_cell *c, const double *yn, double h, double *y)
 {
     const ko_net *n = c->n;
@@ -460,6 +462,117 @@ static double err_norm(const ko_cell *c, const double *y, const double *y2, cons
 #define ADV_OK 0
 #define ADV_FAIL 1
 
+/* TR-BDF2 (Bank et al. 1985), the one-step scheme with one iteration matrix per step:
+ * a trapezoidal stage to t + gamma h, then a BDF2 stage to t + h, gamma = 2 - sqrt(2).
+ * Both stages are y = r + d h f(y) with d = gamma / 2:
+ *   stage 1: r1 = y_n + d h f(y_n)                      -> y_g
+ *   stage 2: r2 = w1 y_g - w0 y_n,  w1 = 1/(gamma(2-gamma)), w0 = (1-gamma)^2/(gamma(2-gamma))
+ *                                                       -> y_{n+1}
+ * The local error y(t+h) - y_{n+1} = C h^3 y''' + O(h^4), C = (-3 gamma^2 + 4 gamma - 2) /
+ * (12 (2 - gamma)), is estimated from the quadratic through f at t, t + gamma h, t + h:
+ *   est = 2 C h (f_n / gamma - f_g / (gamma (1 - gamma)) + f_{n+1} / (1 - gamma)),
+ * where f_g and f_{n+1} follow from the stage equations (f_g = (y_g - y_n)/(d h) - f_n,
+ * f_{n+1} = (y_{n+1} - r2)/(d h)).  Accept when the weighted RMS of est is <= 1; the next
+ * step is h * min(facmax, max(0.2, 0.9 err^(-1/3))).  (Hosea and Shampine 1996 analyse
+ * this pair; their stiff filter of the estimate is not applied.) */
+typedef struct {
+    double g, d, w1, w0, C, a0, a1, a2;
+} trbdf2_coef;
+
+static trbdf2_coef trbdf2_coefficients(void)
+{
+    trbdf2_coef k;
+    k.g = 2.0 - sqrt(2.0);
+    k.d = 0.5 * k.g;
+    k.w1 = 1.0 / (k.g * (2.0 - k.g));
+    k.w0 = (1.0 - k.g) * (1.0 - k.g) / (k.g * (2.0 - k.g));
+    k.C = (-3.0 * k.g * k.g + 4.0 * k.g - 2.0) / (12.0 * (2.0 - k.g));
+    k.a0 = 1.0 / k.g;
+    k.a1 = -1.0 / (k.g * (1.0 - k.g));
+    k.a2 = 1.0 / (1.0 - k.g);
+    return k;
+}
+
+/* One TR-BDF2 step of size h from yn: y1 receives y_{n+1} and est the local error
+ * estimate.  Returns 0, or -1 when a stage's Newton iteration fails. */
+static int trbdf2_step(ko_cell *c, const double *yn, double h, double *y1, double *est)
+{
+    const ko_net *n = c->n;
+    const trbdf2_coef k = trbdf2_coefficients();
+    int N = c->N, i;
+    double f0[KO_MAXN], r[KO_MAXN], yg[KO_MAXN];
+    double T = n->energy ? yn[n->ns] : c->T_iso;
+    if (!(T > 0.0)) return -1;
+    ko_rates(n, T, c->k, c->dk);
+    rhs(n, yn, c->k, c->cvtot, f0);
+    const double dh = k.d * h, inv = 1.0 / dh;
+    for (i = 0; i < N; i++) r[i] = yn[i] + dh * f0[i];
+    for (i = 0; i < N; i++) yg[i] = yn[i];
+    if (be_solve(c, r, dh, yg)) return -1;
+    for (i = 0; i < N; i++) r[i] = k.w1 * yg[i] - k.w0 * yn[i];
+    for (i = 0; i < N; i++) y1[i] = yg[i];
+    if (be_solve(c, r, dh, y1)) return -1;
+    const double ce = 2.0 * k.C * h;
+    for (i = 0; i < N; i++) {
+        double fg = (yg[i] - yn[i]) * inv - f0[i];
+        double f1 = (y1[i] - r[i]) * inv;
+        est[i] = ce * (k.a0 * f0[i] + k.a1 * fg + k.a2 * f1);
+    }
+    return 0;
+}
+
+/* Weighted RMS of the TR-BDF2 estimate, weights atol_i + rtol max(|y_n,i|, |y_{n+1},i|). */
+static double est_norm(const ko_cell *c, const double *yn, const double *y1, const double *est)
+{
+    double s = 0.0;
+    int i;
+    for (i = 0; i < c->N; i++) {
+        double sc = eatol(c, i) + c->o->rtol * fmax(fabs(yn[i]), fabs(y1[i]));
+        double e = est[i] / sc;
+        s += e * e;
+    }
+    return sqrt(s / c->N);
+}
+
+static int advance_trbdf2(ko_cell *c, double *y, double dt, double h0, double facmax, int *nsub)
+{
+    const ko_options *o = c->o;
+    int N = c->N, i;
+    double y1[KO_MAXN], est[KO_MAXN];
+    double t = 0.0, h = h0;
+    int nacc = 0, natt = 0;
+    for (;;) {
+        if (natt >= o->max_substeps) return ADV_FAIL;
+        natt++;
+        int last = 0;
+        if (t + h >= dt * (1.0 - 1e-12)) { h = dt - t; last = 1; }
+        if (trbdf2_step(c, y, h, y1, est)) {
+            h *= 0.5;
+            if (h < o->h_min) return ADV_FAIL;
+            continue;
+        }
+        double err = o->adaptive ? est_norm(c, y, y1, est) : 0.0;
+        if (err <= 1.0) {
+            for (i = 0; i < N; i++) y[i] = y1[i];
+            nacc++;
+            if (last) break;
+            t += h;
+            if (!o->adaptive) continue;
+            double fac = err > 0.0 ? 0.9 / cbrt(err) : facmax;
+            if (fac > facmax) fac = facmax;
+            if (fac < 0.2) fac = 0.2;
+            h *= fac;
+        } else {
+            double fac = 0.9 / cbrt(err);   /* NaN err falls through to the 0.2 clamp */
+            if (!(fac >= 0.2)) fac = 0.2;
+            h *= fac;
+            if (h < o->h_min) return ADV_FAIL;
+        }
+    }
+    *nsub = nacc;
+    return ADV_OK;
+}
+
 /* Advance y over [0, dt] with adaptive sub-steps (or fixed steps when adaptive=0). */
 static int advance(ko_cell *c, double *y, double dt, double h0, double facmax, int *nsub)
 {
@@ -468,6 +581,7 @@ static int advance(ko_cell *c, double *y, double dt, double h0, double facmax, i
     double yf[KO_MAXN], yh[KO_MAXN], y2[KO_MAXN];
     double t = 0.0, h = h0;
     int nacc = 0, natt = 0;
+    if (o->scheme == 1) return advance_trbdf2(c, y, dt, h0, facmax, nsub);
     for (;;) {
         if (natt >= o->max_substeps) return ADV_FAIL;
         natt++;
@@ -710,6 +824,36 @@ int ko_be_step(const ko_net *n, const ko_options *o, const double *yn, double T_
     for (i = 0; i < c->N; i++) y_out[i] = yn[i];
     rc = be_solve(c, yn, h, y_out);
     *n_iter = (int)c->nnewton;
+    free(c);
+    return rc;
+}
+
+/* Post-processing of one state (pins, Sec. 2.2.3): y[0..ns) is clipped and corrected
+ * in place towards the element totals b0[0..ne); returns 0, or -1 when the correction
+ * fails (a relative correction >= 1, an element with no abundance left but a nonzero
+ * defect, or a non-finite result).  y must hold ns + energy entries. */
+int ko_post_process(const ko_net *n, double *y, const double *b0)
+{
+    ko_cell *c = malloc(sizeof *c);
+    int rc;
+    if (!c) return KO_ENOMEM;
+    c->n = n; c->o = NULL; c->N = n->ns + n->energy; c->nnewton = 0;
+    rc = post_process(c, y, b0);
+    free(c);
+    return rc;
+}
+
+/* One TR-BDF2 step of one cell (pins): y_out = y_{n+1}, est_out = the local error
+ * estimate.  Returns 0, or -1 when a stage's Newton iteration fails. */
+int ko_trbdf2_step(const ko_net *n, const ko_options *o, const double *yn, double T_iso,
+                   double cvtot, double h, double *y_out, double *est_out)
+{
+    ko_cell *c = malloc(sizeof *c);
+    int rc;
+    if (!c) return KO_ENOMEM;
+    c->n = n; c->o = o; c->N = n->ns + n->energy; c->T_iso = T_iso; c->cvtot = cvtot;
+    c->atol_s = o->atol; c->nnewton = 0;
+    rc = trbdf2_step(c, yn, h, y_out, est_out);
     free(c);
     return rc;
 }

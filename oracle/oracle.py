@@ -42,14 +42,15 @@ class Options(ctypes.Structure):
                 ("retry_facmax", ctypes.c_double),
                 ("max_substeps", ctypes.c_int), ("max_newton", ctypes.c_int),
                 ("adaptive", ctypes.c_int), ("retry", ctypes.c_int),
-                ("atol_mode", ctypes.c_int), ("guess", ctypes.c_int)]
+                ("atol_mode", ctypes.c_int), ("guess", ctypes.c_int), ("scheme", ctypes.c_int)]
 
 
 def options(tol=None, **kw) -> Options:
     """Options from an ``inputs.Tolerances`` plus keyword overrides."""
     d = dict(rtol=1e-6, atol=1e-10, h_init=1e-6, h_min=1e-30, newton_rtol=1e-12,
              newton_atol_frac=1e-2, facmax=4.0, retry_h_factor=1e-3, retry_facmax=2.0,
-             max_substeps=100000, max_newton=8, adaptive=1, retry=1, atol_mode=0, guess=0)
+             max_substeps=100000, max_newton=8, adaptive=1, retry=1, atol_mode=0, guess=0,
+             scheme=0)
     if tol is not None:
         d.update(rtol=tol.rtol, atol=tol.atol, h_init=tol.h_init, h_min=tol.h_min,
                  max_substeps=tol.max_substeps, max_newton=tol.max_newton,
@@ -80,6 +81,9 @@ def lib():
                                        i32p, i32p, i32p]
             L.ko_be_step.argtypes = [vp, ctypes.POINTER(Options), dp, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, dp, ip]
+            L.ko_post_process.argtypes = [vp, dp, dp]
+            L.ko_trbdf2_step.argtypes = [vp, ctypes.POINTER(Options), dp, ctypes.c_double,
+                                         ctypes.c_double, ctypes.c_double, dp, dp]
             _lib = L
     return _lib
 
@@ -151,6 +155,25 @@ class OracleNetwork:
         rc = lib().ko_be_step(self.ptr, ctypes.byref(opts), _dp(yn), float(T_iso),
                               float(cvtot), float(h), _dp(y), ctypes.byref(it))
         return rc, y, it.value
+
+    def trbdf2_step(self, yn, h, opts: Options, T_iso: float = 300.0, cvtot: float = 1.0):
+        """One TR-BDF2 step: (rc, y_{n+1}, local error estimate)."""
+        yn = np.ascontiguousarray(yn, float)
+        y = np.zeros(self.n)
+        est = np.zeros(self.n)
+        rc = lib().ko_trbdf2_step(self.ptr, ctypes.byref(opts), _dp(yn), float(T_iso),
+                                  float(cvtot), float(h), _dp(y), _dp(est))
+        return rc, y, est
+
+    def post_process(self, y, b0):
+        """Clip + element-total correction of one state (Sec. 2.2.3): (rc, corrected y)."""
+        y = np.array(y, float)
+        if y.shape[0] == self.ns:
+            y = np.append(y, 0.0) if self.energy else y
+        b0 = np.ascontiguousarray(b0, float)
+        assert b0.shape == (self.ne,)
+        rc = lib().ko_post_process(self.ptr, _dp(y), _dp(b0))
+        return rc, y[:self.ns]
 
     def integrate(self, cells, dt: float, opts: Options, nthreads: Optional[int] = None):
         """Integrate SoA cells (``inputs.Cells``) over dt; returns a dict of arrays."""

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 from paper_2504_04941_gb300 import inputs as I
-from _parity import compare, conservation_error
+from _parity import compare, conservation_error, tight_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -56,7 +56,8 @@ def test_robertson_full_parity(kt, oracle_mod, form):
     wl = I.workload(1)
     g = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, kt.options(wl.tol, **form))
     o = ora_run(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol)
-    rep = compare(g, o, wl.network.energy)
+    rep = compare(g, o, wl.network.energy,
+                  tight=tight_oracle(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol, NTHREADS))
     print(rep)
     assert rep.ok(), rep
     assert conservation_error(wl.network, wl.cells.y, g["y"]) <= 1e-12
@@ -71,7 +72,8 @@ def test_combustion_ragged_parity(kt, oracle_mod, form):
     wl = I.workload(2, 250)
     g = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, kt.options(wl.tol, **form))
     o = ora_run(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol)
-    rep = compare(g, o, wl.network.energy)
+    rep = compare(g, o, wl.network.energy,
+                  tight=tight_oracle(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol, NTHREADS))
     print(rep)
     assert rep.ok(), rep
     assert conservation_error(wl.network, wl.cells.y, g["y"]) <= 1e-12
@@ -96,9 +98,10 @@ def test_combustion_full_size_sampled(kt, oracle_mod, form):
     sub = wl.cells.subset(idx)
     o = ora_run(oracle_mod, wl.network, sub, wl.tol.dt, wl.tol)
     gs = {k: (v[:, idx] if v.ndim == 2 else v[idx]) for k, v in g.items()}
-    rep = compare(gs, o, wl.network.energy)
+    rep = compare(gs, o, wl.network.energy,
+                  tight=tight_oracle(oracle_mod, wl.network, sub, wl.tol.dt, wl.tol, NTHREADS))
     print(rep)
-    assert rep.ok(max_flip_frac=0.05), rep
+    assert rep.ok(), rep
     assert conservation_error(wl.network, wl.cells.y, g["y"]) <= 1e-12
 
 
@@ -108,9 +111,10 @@ def test_ism_ragged_parity(kt, oracle_mod, form):
     wl = I.workload(3, 97)
     g = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, kt.options(wl.tol, form=form, persistent=1))
     o = ora_run(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol)
-    rep = compare(g, o, wl.network.energy, rtol=wl.tol.rtol)
+    rep = compare(g, o, wl.network.energy, rtol=wl.tol.rtol,
+                  tight=tight_oracle(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol, NTHREADS))
     print(rep)
-    assert rep.ok(rtol=wl.tol.rtol), rep
+    assert rep.ok(), rep
     assert conservation_error(wl.network, wl.cells.y, g["y"]) <= 1e-12
     assert np.all(g["y"] >= 0)
 
@@ -121,9 +125,10 @@ def test_combined64_ragged_parity(kt, oracle_mod, form):
     wl = I.workload(5, 37)
     g = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, kt.options(wl.tol, form=form, persistent=1))
     o = ora_run(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol)
-    rep = compare(g, o, wl.network.energy, rtol=wl.tol.rtol)
+    rep = compare(g, o, wl.network.energy, rtol=wl.tol.rtol,
+                  tight=tight_oracle(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol, NTHREADS))
     print(rep)
-    assert rep.ok(rtol=wl.tol.rtol), rep
+    assert rep.ok(), rep
     assert conservation_error(wl.network, wl.cells.y, g["y"]) <= 1e-12
     assert np.all(g["y"] >= 0)
 
@@ -142,7 +147,7 @@ def test_edge_cases(kt, oracle_mod):
     one = wl.cells.subset([5])
     g = gpu_run(kt, wl.network, one, 10.0, opts, net)
     o = ora_run(oracle_mod, wl.network, one, 10.0, wl.tol)
-    assert compare(g, o, 0).ok()
+    assert compare(g, o, 0, tight=tight_oracle(oracle_mod, wl.network, one, 10.0, wl.tol, 1)).ok()
     # non-finite and negative inputs, and a cell that must revert
     c = wl.cells
     c.y[0, 1] = np.nan

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 from paper_2504_04941_gb300 import inputs as I
-from _parity import compare
+from _parity import compare, tight_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -72,7 +72,8 @@ def test_autotune_and_cache(kt, oracle_mod, tmp_path):
     g = _direct(kt, net, wl.cells, dt, opts)
     o = oracle_mod.OracleNetwork(wl.network).integrate(wl.cells, dt, oracle_mod.options(wl.tol),
                                                        os.cpu_count())
-    assert compare(g, o, 1).ok()
+    assert compare(g, o, 1, tight=tight_oracle(oracle_mod, wl.network, wl.cells, dt, wl.tol,
+                                               os.cpu_count())).ok()
 
 
 def test_bad_arguments_are_errors_not_faults(kt):

@@ -11,7 +11,7 @@ import pytest
 
 from oracle import mlp_ref as R
 from paper_2504_04941_gb300 import inputs as I
-from _parity import compare
+from _parity import compare, tight_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -143,7 +143,8 @@ def test_untrained_guess_does_not_change_the_answer(kt, oracle_mod):
         g = {k: r[k].cpu().numpy() for k in ("y", "T", "status", "nsub", "nnewton")}
         o = oracle_mod.OracleNetwork(wl.network).integrate(wl.cells, wl.tol.dt,
                                                            oracle_mod.options(wl.tol), os.cpu_count())
-        rep = compare(g, o, 0)
+        rep = compare(g, o, 0, tight=tight_oracle(oracle_mod, wl.network, wl.cells, wl.tol.dt,
+                                                  wl.tol, os.cpu_count()))
         assert rep.ok(), (form, rep)
 
 

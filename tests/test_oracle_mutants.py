@@ -41,15 +41,32 @@ MUTANTS = [
     ("step_full_instead_of_half", "for (i = 0; i < N; i++) y[i] = y2[i];\n            nacc++;",
      "for (i = 0; i < N; i++) y[i] = yf[i];\n            nacc++;"),
     ("half_step_from_wrong_base", "ok = be_solve(c, yh, 0.5 * h, y2) == 0;", "ok = be_solve(c, y, 0.5 * h, y2) == 0;"),
+    ("projection_sign", "y[s] -= y[s] * corr;", "y[s] += y[s] * corr;"),
+    ("no_projection", "y[s] -= y[s] * corr;", ""),
+    ("no_clip", "if (y[s] < 0.0) y[s] = 0.0;", ""),
+    ("projection_no_failure_limit", "if (!(corr < 1.0)) return -1;", ""),
+    ("projection_unweighted", [("m += (double)n->counts[s * ne + e] * n->counts[s * ne + f] * y[s];",
+                                "m += (double)n->counts[s * ne + e] * n->counts[s * ne + f];"),
+                               ("y[s] -= y[s] * corr;", "y[s] -= corr;")], None),
+    ("trbdf2_gamma", "k.g = 2.0 - sqrt(2.0);", "k.g = 2.0 - sqrt(2.1);"),
+    ("trbdf2_w0_sign", "k.w0 = (1.0 - k.g) * (1.0 - k.g) / (k.g * (2.0 - k.g));",
+     "k.w0 = -(1.0 - k.g) * (1.0 - k.g) / (k.g * (2.0 - k.g));"),
+    ("trbdf2_stage2_base", "for (i = 0; i < N; i++) r[i] = k.w1 * yg[i] - k.w0 * yn[i];",
+     "for (i = 0; i < N; i++) r[i] = k.w1 * yg[i] - k.w0 * yg[i];"),
+    ("trbdf2_stage1_no_f0", "for (i = 0; i < N; i++) r[i] = yn[i] + dh * f0[i];",
+     "for (i = 0; i < N; i++) r[i] = yn[i];"),
+    ("trbdf2_estimate_scale", "const double ce = 2.0 * k.C * h;", "const double ce = k.C * h;"),
+    ("trbdf2_estimate_fg_sign", "double fg = (yg[i] - yn[i]) * inv - f0[i];",
+     "double fg = (yg[i] - yn[i]) * inv + f0[i];"),
     ("accept_wrong_norm_weight", "double sc = eatol(c, i) + c->o->rtol * fmax(fabs(y[i]), fabs(y2[i]));",
      "double sc = eatol(c, i) + c->o->rtol * fabs(y[i]) * 1e3;"),
 ]
 # Equivalent mutants, left out on purpose: they change nothing any pin (or any user)
 # can observe.  A different growth law (0.9/err instead of 0.9/sqrt(err), or err^2 in
-# place of err) is another valid controller of the same order; the post-processing
-# clip and the sign of the element projection act on rounding-level defects only,
-# because every Newton update of backward Euler conserves the linear invariants
-# exactly (N J = 0 implies N delta = -N G).
+# place of err) is another valid controller of the same order.  Inside an integration
+# the element projection acts on rounding-level defects only (every Newton update of
+# backward Euler conserves the linear invariants exactly, N J = 0 implies
+# N delta = -N G), so its mutants are caught by the direct post-processing pin.
 
 
 def _load_variant(tmpdir, name, old, new):
@@ -192,7 +209,36 @@ def _pins(m):
         r = m.OracleNetwork(wl.network).integrate(cells, 1e-3, m.options(wl.tol), 1)
         return np.all(r["y"] >= 0) and abs(r["y"][:, 0].sum() - 1.0) < 1e-14
 
-    for name, fn in (("lu_exact", lu_exact), ("lu_pivot", lu_pivot), ("jac_fd", jac_fd),
+    def post_process():
+        # hand-solved cases of the least relative change (see test_oracle_pins)
+        h2 = m.OracleNetwork(I._irreversible("h_h2", ["H", "H2"], ["H"], [1.0, 2.0], [0.0, 0.0],
+                                             [1.0, 1.0], [[1], [2]], 0, 300.0, 10.0, 1e5,
+                                             [((0, 0), (1,), 1.0, 0.0, 0.0, -1)]))
+        rc, y = h2.post_process([0.5, 0.25], [0.999])
+        ok = rc == 0 and np.allclose(y, [0.5 - 1 / 3000, 0.25 - 1 / 3000], rtol=1e-14, atol=0)
+        rc, y = h2.post_process([0.5, -1e-6], [0.5])
+        ok = ok and rc == 0 and y[1] == 0.0 and y[0] == 0.5
+        rc, _ = h2.post_process([0.5, 0.25], [0.1])
+        return ok and rc != 0
+
+    def trbdf2():
+        from scipy.linalg import expm
+        k1, k2 = 3.0, 7.0
+        net = m.OracleNetwork(I.decay_chain_network(k1, k2))
+        K = np.array([[-k1, 0, 0], [k1, -k2, 0], [0, k2, 0]])
+        y0 = np.array([0.9, 0.1, 0.0])
+        errs = []
+        for h in (0.02, 0.01):
+            cells = I.Cells(y0.reshape(3, 1).copy(), np.array([300.0]), np.array([1.0]))
+            r = net.integrate(cells, 1.0, m.options(atol=1e-16, h_init=h, adaptive=0, retry=0,
+                                                   newton_rtol=1e-15, scheme=1), 1)
+            errs.append(np.abs(r["y"][:, 0] - expm(K) @ y0).max())
+        rc, y1, est = net.trbdf2_step(y0, 2.5e-3, m.options(atol=1e-16, newton_rtol=1e-15, scheme=1))
+        true = expm(K * 2.5e-3) @ y0 - y1
+        return (3.7 < errs[0] / errs[1] < 4.3 and rc == 0 and
+                bool(np.all(np.abs(est / true - 1.0) < 0.04)))
+
+    for name, fn in (("lu_exact", lu_exact), ("post_process", post_process), ("trbdf2", trbdf2), ("lu_pivot", lu_pivot), ("jac_fd", jac_fd),
                      ("rhs_robertson", rhs_robertson), ("rates_printed", rates_printed),
                      ("fixed_step_chain", fixed_step_chain), ("bateman", bateman),
                      ("single_step_two_halves", single_step_two_halves),

@@ -391,3 +391,241 @@ def test_network_element_imbalance_rejected(oracle_mod, tmp_path):
     net.write(p)
     with pytest.raises(ValueError):
         oracle_mod.OracleNetwork(p)
+
+
+# ------------------------------------------------------------------ post-processing
+#
+# Sec. 2.2.3: negative abundances are clipped, then the element totals b0 of the
+# initial state are restored.  The correction is read as the least change of the
+# abundances, measured relative to each abundance: minimise sum_s dy_s^2 / y_s
+# subject to N (y + dy) = b0.  Its Lagrange condition makes dy_s / y_s a combination
+# of the element columns of species s, dy_s = -y_s (N^T lambda)_s, and the constraint
+# fixes lambda.  The cases below are solved by hand from that definition.
+
+
+def _h_h2_network():
+    """One element H; species H (1 atom) and H2 (2 atoms); H + H -> H2."""
+    return I._irreversible("h_h2", ["H", "H2"], ["H"], [1.0, 2.0], [0.0, 0.0], [1.0, 1.0],
+                           [[1], [2]], 0, 300.0, 10.0, 1e5, [((0, 0), (1,), 1.0, 0.0, 0.0, -1)])
+
+
+def _h_o_network():
+    """Elements H, O; species H, O, OH, H2O; H + O -> OH, H + OH -> H2O."""
+    return I._irreversible("h_o", ["H", "O", "OH", "H2O"], ["H", "O"], [1.0, 16.0, 17.0, 18.0],
+                           [0.0] * 4, [1.0] * 4, [[1, 0], [0, 1], [1, 1], [2, 1]], 0, 300.0,
+                           10.0, 1e5, [((0, 1), (2,), 1.0, 0.0, 0.0, -1),
+                                       ((0, 2), (3,), 1.0, 0.0, 0.0, -1)])
+
+
+def test_post_process_one_element_hand_solved(oracle_mod):
+    """y = (H 0.5, H2 0.25) carries 1.0 H atoms against b0 = 0.999.  Then
+    lambda = (1.0 - 0.999) / (1*0.5 + 4*0.25) = 1/1500 and
+    y' = (0.5 (1 - 1/1500), 0.25 (1 - 2/1500)) = (0.5 - 1/3000, 0.25 - 1/3000)."""
+    net = oracle_mod.OracleNetwork(_h_h2_network())
+    rc, y = net.post_process([0.5, 0.25], [0.999])
+    assert rc == 0
+    exact = [Fraction(1, 2) - Fraction(1, 3000), Fraction(1, 4) - Fraction(1, 3000)]
+    for got, ref in zip(y, exact):
+        assert abs(Fraction(got) - ref) <= 8 * EPS * ref
+    assert abs(y[0] + 2 * y[1] - 0.999) <= 4 * EPS
+
+
+def test_post_process_two_elements_hand_solved(oracle_mod):
+    """y = (H 1/2, O 1/4, OH 1/8, H2O 1/16) and lambda = (2^-10, -2^-9) chosen first.
+    N y = (3/4, 7/16); N diag(y) N^T = [[7/8, 1/4], [1/4, 7/16]], so its product with
+    lambda is (3/8, -5/8)/1024 and b0 = (3/4 - 3/8192, 7/16 + 5/8192).  The answer is
+    y_s (1 - (N^T lambda)_s) = (1/2 - 1/2048, 1/4 + 1/2048, 1/8 + 1/8192, 1/16): every
+    number here is a short binary fraction, exact in FP64."""
+    net = oracle_mod.OracleNetwork(_h_o_network())
+    b0 = [0.75 - 0.375 / 1024, 0.4375 + 0.625 / 1024]
+    rc, y = net.post_process([0.5, 0.25, 0.125, 0.0625], b0)
+    assert rc == 0
+    ref = np.array([0.5 - 0.5 / 1024, 0.25 + 0.5 / 1024, 0.125 + 0.125 / 1024, 0.0625])
+    assert np.all(np.abs(y - ref) <= 8 * EPS * ref)
+
+
+def test_post_process_clip_keeps_clipped_species_at_zero(oracle_mod):
+    """A negative abundance is set to 0 and, being weighted by its own value, stays 0;
+    the other species carry the whole correction."""
+    net = oracle_mod.OracleNetwork(_h_o_network())
+    y_in = np.array([0.5, -1e-6, 0.125, 0.0625])
+    b0 = np.array([0.75 * (1 + 1e-3), 0.1875 * (1 - 2e-3)])
+    rc, y = net.post_process(y_in, b0)
+    assert rc == 0
+    assert y[1] == 0.0
+    counts = np.array([[1, 0], [0, 1], [1, 1], [2, 1]], float)
+    assert np.all(np.abs(counts.T @ y - b0) <= 4 * EPS * b0)
+
+
+@pytest.mark.parametrize("wid", [2, 3, 5])
+def test_post_process_is_the_least_relative_change(oracle_mod, wid):
+    """Random states of the workload networks with an O(1e-3) element defect and one
+    clipped negative: the totals come back to 1e-14, and the result equals the
+    minimum-norm solution of the scaled constraint (N W)(z) = b0 - N y, dy = W z with
+    W = diag(sqrt(y)), computed independently through numpy's SVD pseudo-inverse."""
+    netw = I.network(wid)
+    net = oracle_mod.OracleNetwork(netw)
+    rng = np.random.default_rng(wid)
+    Nm = netw.counts.T.astype(float)
+    for trial in range(5):
+        y = 10.0 ** rng.uniform(-12, 0, netw.ns)
+        y[rng.integers(netw.ns)] = -1e-14
+        yc = np.maximum(y, 0.0)
+        b0 = Nm @ yc * (1.0 + 1e-3 * rng.uniform(-1, 1, netw.ne))
+        rc, got = net.post_process(y, b0)
+        assert rc == 0
+        assert np.all(np.abs(Nm @ got - b0) <= 1e-14 * b0)
+        W = np.sqrt(yc)
+        z = np.linalg.pinv(Nm * W[None, :]) @ (b0 - Nm @ yc)
+        ref = yc + W * z
+        # the SVD route is accurate relative to the correction it computes
+        assert np.all(np.abs(got - ref) <= 1e-9 * np.abs(ref - yc) + 8 * EPS * yc + 1e-300)
+        assert np.all(got >= 0.0)
+
+
+def test_post_process_failure_rules(oracle_mod):
+    """A correction that would remove 100 % or more of a species fails, as does a
+    defect in an element that no species holds any more; a zero defect there is fine."""
+    h2 = oracle_mod.OracleNetwork(_h_h2_network())
+    # lambda = 0.6: H2 would lose 2*0.6 = 120 % of itself
+    rc, _ = h2.post_process([0.5, 0.25], [1.0 - 0.6 * 1.5])
+    assert rc != 0
+    # lambda = 0.45: H keeps 55 %, H2 10 %
+    rc, y = h2.post_process([0.5, 0.25], [1.0 - 0.45 * 1.5])
+    assert rc == 0
+    assert y == pytest.approx([0.5 * 0.55, 0.25 * 0.1], rel=1e-14)
+    ho = oracle_mod.OracleNetwork(_h_o_network())
+    rc, _ = ho.post_process([0.5, 0.0, 0.0, 0.0], [0.5, 1e-3])
+    assert rc != 0
+    rc, y = ho.post_process([0.5, 0.0, 0.0, 0.0], [0.5 * (1 - 1e-3), 0.0])
+    assert rc == 0
+    assert y == pytest.approx([0.5 * (1 - 1e-3), 0.0, 0.0, 0.0], rel=1e-14)
+
+
+# ------------------------------------------------------------------ TR-BDF2 (second scheme)
+#
+# The one-step scheme with one iteration matrix per step (Bank et al. 1985): a
+# trapezoidal stage to t + gamma h and a BDF2 stage to t + h, gamma = 2 - sqrt(2).  On a
+# linear system y' = K y each stage is one linear solve with I - d h K, d = gamma/2.
+
+GAMMA = 2.0 - math.sqrt(2.0)
+
+
+def _chain(k1=2.0, k2=50.0):
+    K = np.array([[-k1, 0, 0], [k1, -k2, 0], [0, k2, 0]])
+    return I.decay_chain_network(k1, k2), K
+
+
+def _trbdf2_linear(K, y, h):
+    """One TR-BDF2 step on y' = K y written as two linear solves."""
+    g, d = GAMMA, GAMMA / 2
+    A = np.eye(len(y)) - d * h * K
+    yg = np.linalg.solve(A, (np.eye(len(y)) + d * h * K) @ y)
+    w1, w0 = 1 / (g * (2 - g)), (1 - g) ** 2 / (g * (2 - g))
+    return np.linalg.solve(A, w1 * yg - w0 * y)
+
+
+def test_trbdf2_fixed_step_linear_chain(oracle_mod):
+    netw, K = _chain()
+    net = oracle_mod.OracleNetwork(netw)
+    y0 = np.array([0.7, 0.2, 0.1])
+    cells = I.Cells(y0.reshape(3, 1).copy(), np.array([300.0]), np.array([1.0]))
+    r = net.integrate(cells, 1.0, oracle_mod.options(atol=1e-14, h_init=0.01, adaptive=0, retry=0,
+                                                     newton_rtol=1e-14, scheme=1), 1)
+    ref = y0.copy()
+    for _ in range(100):
+        ref = _trbdf2_linear(K, ref, 0.01)
+    assert r["nsub"][0] == 100
+    assert np.allclose(r["y"][:, 0], ref, rtol=1e-13, atol=1e-16)
+
+
+def test_trbdf2_is_second_order(oracle_mod):
+    """Fixed steps against the exact solution expm(K t) y0: halving h divides the error
+    by 4 (backward Euler would divide it by 2)."""
+    from scipy.linalg import expm
+    netw, K = _chain(3.0, 7.0)
+    net = oracle_mod.OracleNetwork(netw)
+    y0 = np.array([0.9, 0.1, 0.0])
+    exact = expm(K * 1.0) @ y0
+    errs = []
+    for h in (0.02, 0.01, 0.005):
+        cells = I.Cells(y0.reshape(3, 1).copy(), np.array([300.0]), np.array([1.0]))
+        r = net.integrate(cells, 1.0, oracle_mod.options(atol=1e-16, h_init=h, adaptive=0, retry=0,
+                                                         newton_rtol=1e-15, scheme=1), 1)
+        errs.append(np.abs(r["y"][:, 0] - exact).max())
+    assert 3.7 < errs[0] / errs[1] < 4.3 and 3.7 < errs[1] / errs[2] < 4.3, errs
+
+
+def test_trbdf2_estimate_is_the_local_error(oracle_mod):
+    """One step from y0: the estimate equals expm(h K) y0 - y1 to leading order, so
+    its ratio to the true local error tends to 1 as h shrinks."""
+    from scipy.linalg import expm
+    netw, K = _chain(3.0, 7.0)
+    net = oracle_mod.OracleNetwork(netw)
+    y0 = np.array([0.9, 0.1, 0.0])
+    opts = oracle_mod.options(atol=1e-16, newton_rtol=1e-15, scheme=1)
+    for h, tol in ((1e-2, 0.15), (2.5e-3, 0.04)):
+        rc, y1, est = net.trbdf2_step(y0, h, opts)
+        assert rc == 0
+        true = expm(K * h) @ y0 - y1
+        assert np.all(np.abs(est / true - 1.0) < tol), (h, est, true)
+
+
+def test_trbdf2_adaptive_bateman_accuracy(oracle_mod):
+    """Adaptive TR-BDF2 on A -> B -> C against the Bateman closed form.  The control
+    keeps the local error per step near rtol, so steps scale like rtol^(1/3) and a
+    second-order method's global error like h^2 ~ rtol^(2/3): slope 2/3 in log-log (the
+    first-order scheme's is 1/2), and the error stays below 2 rtol^(2/3)."""
+    net = oracle_mod.OracleNetwork(I.decay_chain_network(1.0, 10.0))
+    cells = I.Cells(np.array([[1.0], [0.0], [0.0]]), np.array([300.0]), np.array([1.0]))
+    A = math.exp(-2.0)
+    B = 1 / 9 * (math.exp(-2.0) - math.exp(-20.0))
+    ref = np.array([A, B, 1 - A - B])
+    errs, nsub = [], []
+    for rtol in (1e-4, 1e-6, 1e-8):
+        r = net.integrate(cells, 2.0, oracle_mod.options(rtol=rtol, atol=1e-14, h_init=1e-6, scheme=1), 1)
+        errs.append(np.abs(r["y"][:, 0] / ref - 1).max())
+        nsub.append(int(r["nsub"][0]))
+    for e, rtol in zip(errs, (1e-4, 1e-6, 1e-8)):
+        assert e <= 2.0 * rtol ** (2 / 3), errs
+    for a, b in zip(errs, errs[1:]):
+        assert 0.6 <= math.log10(a / b) / 2 <= 0.73, errs
+    # the step count grows like rtol^(-1/3): x100 tighter -> ~4.6x the steps
+    assert 3.0 < nsub[1] / nsub[0] < 7.0 and 3.0 < nsub[2] / nsub[1] < 7.0, nsub
+
+
+def test_trbdf2_robertson_vs_radau(oracle_mod):
+    from scipy.integrate import solve_ivp
+    wl = I.workload(1, 3)
+    net = oracle_mod.OracleNetwork(wl.network)
+    r = net.integrate(wl.cells, 1e4, oracle_mod.options(wl.tol, scheme=1), 1)
+    assert np.all(r["status"] == 0)
+    for c in range(3):
+        y0 = wl.cells.y[:, c]
+
+        def f(t, y):
+            return [-0.04 * y[0] + 1e4 * y[1] * y[2], 0.04 * y[0] - 1e4 * y[1] * y[2] - 3e7 * y[1] ** 2,
+                    3e7 * y[1] ** 2]
+        ref = solve_ivp(f, (0, 1e4), y0, method="Radau", rtol=1e-13, atol=1e-20).y[:, -1]
+        assert np.abs(r["y"][:, c] / ref - 1).max() <= 1e-4
+        assert abs(r["y"][:, c].sum() - y0.sum()) <= 1e-14
+
+
+@pytest.mark.parametrize("wid", [2, 3])
+def test_trbdf2_conservation(oracle_mod, wid):
+    """Both stages are combinations of states and rates, so the element totals and the
+    energy invariant are kept to rounding, as with backward Euler."""
+    wl = I.workload(wid, 4)
+    netw = wl.network
+    net = oracle_mod.OracleNetwork(netw)
+    r = net.integrate(wl.cells, wl.tol.dt, oracle_mod.options(wl.tol, scheme=1), 2)
+    assert np.all(r["status"] == 0)
+    y0 = np.maximum(wl.cells.y, 0.0)
+    b0, b1 = netw.counts.T @ y0, netw.counts.T @ r["y"]
+    assert np.all(np.abs(b1 - b0) <= 1e-12 * b0)
+    assert np.all(r["y"] >= 0.0)
+    if netw.energy:
+        cv = netw.cv @ y0
+        E0 = cv * wl.cells.T + netw.h @ y0
+        E1 = cv * r["T"] + netw.h @ r["y"]
+        assert np.all(np.abs(E1 - E0) <= 1e-12 * (cv * wl.cells.T + np.abs(netw.h) @ y0))
