@@ -37,15 +37,29 @@ from paper_2504_04941_gb300 import shard  # noqa: E402
 METRIC = ("cell-integrations/s over fixed Δt at 1e-6 rel error vs FP64 oracle; "
           "plain vs chosen form")
 UNIT = "cell-integrations/s"
-# FP64 pipe of GB300: 152 SMs x 2 FP64 FMA/clk/SM x 2 flop x 2.07 GHz = 1.26 TFLOP/s
-# (nominal 1.25 TFLOP/s); FP32: 152 x 128 FMA/clk x 2 x 2.07 GHz = 80.5 TFLOP/s.
-FP64_PEAK_TFLOPS = 1.25
-FP32_PEAK_TFLOPS = 80.5
+# Nominal pipes of GB300 (context; the roofline uses the peaks measured in the run by
+# kt_fma_peak): FP64 152 SMs x 2 FMA/clk x 2 flop x 2.07 GHz = 1.26 TFLOP/s,
+# FP32 152 x 128 FMA/clk x 2 x 2.07 GHz = 80.5 TFLOP/s.
+FP64_NOMINAL_TFLOPS = 1.25
+FP32_NOMINAL_TFLOPS = 80.5
 # DRAM bytes (read + write) per cell of one launch of the chosen-form lane kernel on the
-# combustion10 network, from the ncu capture summarised in
-# profiles/lane_kernel_fp32lu_combustion10_65536cells_dt1e-10.md (6.945 MB for 65,536
-# cells; per-cell state lives in shared memory, so the traffic does not grow with dt)
-LANE_COMBUSTION10_DRAM_BYTES_PER_CELL = 6945024 / 65536
+# combustion network, from an ncu capture of the kernel built from the sources whose
+# hash is the key (a different build reports traffic null until it is captured again).
+LANE_TRAFFIC_BYTES_PER_CELL = {}
+
+
+def kernel_source_hash() -> str:
+    """sha256 (16 hex digits) of the CUDA sources and the C header the library is built from."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2504_04941_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, fn), "rb") as f:
+                h.update(fn.encode() + b"\0" + f.read())
+    with open(os.path.join(ROOT, "include", "kt.h"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 # ------------------------------------------------------------------ work counts
@@ -228,7 +242,8 @@ def reference_arm(args):
             "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             # the GPU arm's workload; each step times a bounded sample of its cells
-            "config": config_of(args, wl, args.ncells or I.FULL_CELLS[args.workload]),
+            "config": dict(config_of(args, wl, args.ncells or I.FULL_CELLS[args.workload]),
+                           timed_cells_per_step=n),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                              "sample": f"{n} cells of the {wl.name} workload per step (same "
                                        f"network, tolerances and dt), pthreads over cells"},
@@ -317,13 +332,21 @@ def main():
         for f in ("cells_per_warp", "persistent", "block_warps", "blocks_per_sm"):
             forms["chosen"][f] = int(getattr(topts, f))
     state = kt.State(net, ncells)
+    zero_cost = torch.zeros(ncells, dtype=torch.int32, device=dev)
     results = {}
     clocks = ClockSampler(local)
     clock_started = False
+    # measured peaks of the FP64 and FP32 pipes (kt_fma_peak, ~0.5 s each, best of 3)
+    peaks = {"fp64_tflops": kt.fma_peak(False), "fp32_tflops": kt.fma_peak(True)}
+    cost = {"next": None}
+
     def run_step(name, opts):
         if forms[name].get("use_graph"):
-            # the library-owned state replays a captured graph (scratch reset + kernel);
-            # each step integrates the same input batch, copied in device to device
+            # the library-owned state replays a captured graph (queue order + kernel);
+            # each step integrates the same input batch, copied in device to device,
+            # with the cost estimate the longest-first order reads
+            if forms[name].get("schedule") and cost["next"] is not None:
+                state.set_cost(cost["next"])
             state.upload(y_in, T_in, rho)
             state.integrate(wl.tol.dt, opts)
         else:
@@ -335,6 +358,9 @@ def main():
         # the plain form is a context line timed once without warm-up (one launch of
         # tens of seconds; module load and attribute setup are microseconds of it)
         nwarm = args.warmup if name == "chosen" else 0
+        sched = bool(forms[name].get("schedule"))
+        if sched:
+            state.set_cost(zero_cost)          # the first warm-up runs without a cost history
         warm_ms = []
         for _ in range(nwarm):
             w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -343,6 +369,13 @@ def main():
             w1.record(stream)
             torch.cuda.synchronize()
             warm_ms.append(w0.elapsed_time(w1))
+        if sched:
+            # cost estimate of an operator-split simulation: the Newton counts of the next
+            # interval (the batch's end state advanced by dt once more), not of the timed
+            # interval itself.  The state holds y(dt) after the warm-ups.
+            state.integrate(wl.tol.dt, opts)
+            nxt = state.download()["nnewton"]
+            cost["next"] = torch.from_numpy(nxt.copy()).to(dev)
         kt.check_scratch(scratch)
         state.check()
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -374,17 +407,13 @@ def main():
         nsub = out["nsub"].to(torch.int64).sum().item()
         st = out["status"].cpu().numpy()
         f64, f32, trans = flops_per_newton(wl.network, forms[name]["form"])
-        # factorisations: count one per Newton solve start and per refresh (upper bound
-        # of the FP32 work is not needed; the FP64 work is per iteration)
         per_launch_ms = tot_ms / nsteps
         results[name] = {
             "steps": nsteps, "warmup": nwarm,
-            # warm-up launches: the first runs without a cost history (the longest-first
-            # queue order comes from the previous call's Newton counts)
-            "warmup_ms": warm_ms,
             "options": {k: int(v) for k, v in forms[name].items()},
             "value": shard.weak_throughput(ncells, world, nsteps, tot_ms / 1e3),
             "ms_per_step": per_launch_ms,
+            "step_ms": step_ms,
             "wall_s": wall,
             "newton_iters": int(nnew), "substeps": int(nsub),
             "status_counts": {int(k): int(v) for k, v in zip(*np.unique(st, return_counts=True))},
@@ -393,6 +422,25 @@ def main():
             "exp_per_s": float(nnew) * trans / (per_launch_ms / 1e3),
             "fp32_flops_per_factorisation": f32,
         }
+        if forms[name]["form"] == kt.KT_FORM_FP32LU:
+            # FP32 work with the counts the kernel keeps: a triangular solve per Newton
+            # iteration, and per accepted sub-step at least one Jacobian and two
+            # factorisations (h and h/2); rejected attempts and refreshes add more
+            N = wl.network.n
+            lu, solve = _lu_flops(N), 2 * N * N - N
+            jac32 = f32 - (2 * N * N + lu + solve)
+            results[name]["fp32_flops_lower_bound"] = float(nnew * solve + nsub * (jac32 + 2 * (2 * N * N + lu)))
+        if sched:
+            # warm-up 1 has no cost history (index order); later warm-ups order the queue
+            # by the exact counts of the same integration (perfect foresight, a bound no
+            # caller reaches); the timed steps use the next interval's counts
+            results[name].update({
+                "cold_ms": warm_ms[0] if warm_ms else None,
+                "foresight_ms": min(warm_ms[1:]) if len(warm_ms) > 1 else None,
+                "perturbed_ms": per_launch_ms,
+                "history": "Newton counts of the following interval (end state advanced by dt)"})
+        else:
+            results[name]["warmup_ms"] = warm_ms
     clk = clocks.stop() if clock_started else {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
 
     head = results.get("chosen") or results.get("plain")
@@ -410,11 +458,17 @@ def main():
                   status=torch.empty(ncells, dtype=torch.int32).pin_memory().numpy(),
                   nsub=torch.empty(ncells, dtype=torch.int32).pin_memory().numpy(),
                   nnewton=torch.empty(ncells, dtype=torch.int32).pin_memory().numpy())
+        # the cost estimate of the longest-first order comes from the host too, like the
+        # inputs (an operator-split caller would pass its previous step's counts)
+        use_cost = bool(forms[head_name].get("schedule")) and cost["next"] is not None
+        hc = cost["next"].cpu().pin_memory().numpy() if use_cost else None
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
+            if use_cost:
+                state.set_cost(hc)
             state.upload(hy, hT, hr)
             state.integrate(wl.tol.dt, opts)
             state.download(out=ho)
@@ -423,7 +477,7 @@ def main():
         e2e_s = shard.max_over_ranks(e2e_s, dev)
         ns = wl.network.ns
         e2e = {"value": shard.weak_throughput(ncells, world, args.e2e_steps, e2e_s), "unit": UNIT, "steps": args.e2e_steps,
-               "h2d_bytes_per_step": ncells * (ns + 2) * 8,
+               "h2d_bytes_per_step": ncells * (ns + 2) * 8 + (ncells * 4 if use_cost else 0),
                "d2h_bytes_per_step": ncells * (ns + 1) * 8 + 3 * ncells * 4}
 
     # ---- CPU baseline: the oracle on a bounded sample of the batch (rank 0, one GPU
@@ -450,19 +504,27 @@ def main():
 
     if rank == 0:
         r = head
-        traffic = (LANE_COMBUSTION10_DRAM_BYTES_PER_CELL * ncells
-                   if args.workload == 2 and head_name == "chosen" else None)
+        per_cell = LANE_TRAFFIC_BYTES_PER_CELL.get(kernel_source_hash())
+        traffic = (per_cell * ncells if per_cell and args.workload == 2 and head_name == "chosen"
+                   else None)
         hbm_peak, hbm_src = hbm_peak_gbs()
         hbm_gbs = traffic / (r["ms_per_step"] * 1e-3) / 1e9 if traffic else None
-        roof = {"bound": "alu", "achieved": r["fp64_tflops"], "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": r["fp64_tflops"] / FP64_PEAK_TFLOPS, "traffic": traffic,
+        p64, p32 = peaks["fp64_tflops"], peaks["fp32_tflops"]
+        roof = {"bound": "alu", "achieved": r["fp64_tflops"], "peak": p64,
+                "unit": "TFLOP/s", "frac": r["fp64_tflops"] / p64, "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum)",
-                "pipe": "fp64", "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz "
-                                               "(nominal 1.25 TFLOP/s)",
+                "pipe": "fp64",
+                "peak_source": "measured in this run: kt_fma_peak FP64 FMA loop, best of 3 (of measured)",
+                "fp64_nominal_tflops": FP64_NOMINAL_TFLOPS,
+                "fp32_peak_tflops": p32, "fp32_peak_source": "measured in this run: kt_fma_peak FP32 FMA loop",
                 # the same launch against HBM: evidence that the path is not memory bound
                 "hbm_gbs": hbm_gbs, "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src,
                 "hbm_frac": hbm_gbs / hbm_peak if hbm_gbs else None,
+                "kernel_source_hash": kernel_source_hash(),
                 "kernel": f"{'lane_kernel' if wl.network.n <= 16 else 'warp_kernel'} ({head_name} form)"}
+        if head_name == "chosen" and "fp32_flops_lower_bound" in r:
+            roof["fp32_achieved_tflops"] = r["fp32_flops_lower_bound"] / (r["ms_per_step"] * 1e-3) / 1e12
+            roof["fp32_frac"] = roof["fp32_achieved_tflops"] / p32
         line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,

@@ -137,6 +137,15 @@ KT_API int kt_state_create(const kt_network *net, int64_t ncells, kt_state **out
 KT_API int kt_state_upload(kt_state *st, const double *y, const double *T, const double *rho,
                     int src_is_device, void *cuda_stream);
 
+/* Set the per-cell cost estimate that the longest-first queue order (opts->schedule)
+ * reads: cost [ncells] int32 (host or device), e.g. the Newton counts of the previous
+ * step of an operator-split simulation, or any estimate the caller has.  It is copied
+ * into the state's n_newton counters, which every kt_integrate overwrites with the
+ * counts it measured.  The order changes no result, only the load balance (a
+ * scheduling aid of this library; the paper has no counterpart).  Asynchronous on
+ * stream, same source rules as kt_state_upload. */
+KT_API int kt_state_set_cost(kt_state *st, const int32_t *cost, int src_is_device, void *cuda_stream);
+
 /* Advance every cell of the state by dt in place (asynchronous on stream).  With
  * opts->use_graph the call (scratch reset + kernel) is captured once into a CUDA graph
  * on a private stream and replayed on `stream` while dt and *opts are unchanged. */
@@ -272,6 +281,15 @@ KT_API int kt_network_attach_mlp(kt_network *net, const kt_mlp *mlp);
 /* Diagnostics: out[i] = exp(x[i]) for device arrays, which = 0 CUDA's exp, 1 the
  * library's table-driven exponential (valid for -708 <= x <= 709). */
 KT_API int kt_debug_exp(const double *x, double *out, int64_t n, int which, void *cuda_stream);
+
+/* Diagnostics: peak probe of the FP64 (fp32 = 0) or FP32 (fp32 = 1) pipe, the
+ * denominator of the library's roofline figures.  Launches `blocks` blocks (0: 8 per
+ * SM) of 256 threads, each thread running 8 independent fused multiply-add chains for
+ * `iters` rounds; *flops (host, may be NULL) receives the flops launched
+ * (2 x 8 x iters x threads).  The caller times the launch on `stream` with events.
+ * sink: device buffer of at least 8 bytes, written only to keep the loop alive. */
+KT_API int kt_fma_peak(int fp32, int64_t iters, int blocks, double *sink, void *cuda_stream,
+                       double *flops);
 
 /* Thread-local message of the last failed call ("" if none). */
 KT_API const char *kt_last_error(void);

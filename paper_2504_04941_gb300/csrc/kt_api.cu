@@ -648,6 +648,16 @@ int kt_state_upload(kt_state *st, const double *y, const double *T, const double
     return KT_OK;
 }
 
+int kt_state_set_cost(kt_state *st, const int32_t *cost, int src_is_device, void *cuda_stream)
+{
+    if (!st || !cost) return fail(KT_EINVAL, "kt_state_set_cost: NULL argument");
+    if (st->ncells == 0) return KT_OK;
+    const cudaMemcpyKind k = src_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    cudaError_t e = cudaMemcpyAsync(st->nnew, cost, static_cast<size_t>(st->ncells) * sizeof(int32_t), k,
+                                    static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? KT_OK : cuda_fail(e, "kt_state_set_cost");
+}
+
 int kt_integrate(kt_state *st, double dt, const kt_options *opts, void *cuda_stream)
 {
     if (!st) return fail(KT_EINVAL, "kt_integrate: NULL state");

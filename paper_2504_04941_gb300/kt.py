@@ -68,6 +68,7 @@ def lib():
         L.kt_integrate.argtypes = [vp, ctypes.c_double, ctypes.POINTER(Options), vp]
         L.kt_state_download.argtypes = [vp, dptr, dptr, dptr, dptr, dptr, c_int, vp]
         L.kt_state_check.argtypes = [vp, vp]
+        L.kt_state_set_cost.argtypes = [vp, dptr, c_int, vp]
         L.kt_state_free.argtypes = [vp]
         L.kt_state_free.restype = None
         L.kt_scratch_bytes.restype = ctypes.c_size_t
@@ -97,6 +98,7 @@ def lib():
         L.kt_mlp_load.argtypes = [vp, ctypes.c_char_p]
         L.kt_network_attach_mlp.argtypes = [vp, vp]
         L.kt_debug_exp.argtypes = [dptr, dptr, c_i64, c_int, vp]
+        L.kt_fma_peak.argtypes = [c_int, c_i64, c_int, dptr, vp, ctypes.POINTER(ctypes.c_double)]
         L.kt_integrate_noalloc.argtypes = [vp, c_i64, dptr, dptr, dptr, ctypes.c_double,
                                            ctypes.POINTER(Options), dptr, dptr, dptr, dptr, dptr, vp]
         _lib = L
@@ -315,6 +317,18 @@ class State:
     def integrate(self, dt: float, opts: Options, stream=None):
         _check(lib().kt_integrate(self.ptr, float(dt), ctypes.byref(opts), _stream_handle(stream)))
 
+    def set_cost(self, cost, stream=None):
+        """Per-cell cost estimate for the longest-first queue order (int32 [ncells],
+        numpy array or CUDA tensor); the next integrate overwrites it with its counts."""
+        dev = hasattr(cost, "data_ptr") and getattr(cost, "is_cuda", False)
+        if dev:
+            _require(cost, "cost", (self.ncells,), "int32")
+            p = _ptr(cost)
+        else:
+            _require_host(cost, "cost", (self.ncells,), np.int32)
+            p = _np_ptr(cost)
+        _check(lib().kt_state_set_cost(self.ptr, p, int(dev), _stream_handle(stream)))
+
     def download(self, stream=None, out=None):
         """Copy results into host numpy arrays (synchronises; raises on device errors)."""
         ns, nc = self.net.ns, self.ncells
@@ -497,6 +511,34 @@ def debug_exp(x, which: int, stream=None):
     out = torch.empty_like(x)
     _check(lib().kt_debug_exp(_ptr(x), _ptr(out), x.numel(), int(which), _stream_handle(stream)))
     return out
+
+
+def fma_peak(fp32: bool, seconds: float = 0.5, repeats: int = 3) -> float:
+    """Measured FMA throughput of the FP64 (or FP32) pipe in TFLOP/s: kt_fma_peak
+    timed with CUDA events on the current stream, best of `repeats` launches of about
+    `seconds` each (the first, short launch calibrates the length)."""
+    import torch
+    sink = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    h = ctypes.c_void_p(stream.cuda_stream)
+
+    def once(iters):
+        flops = ctypes.c_double()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        _check(lib().kt_fma_peak(int(bool(fp32)), int(iters), 0, _ptr(sink), h, ctypes.byref(flops)))
+        b.record(stream)
+        b.synchronize()
+        return flops.value, a.elapsed_time(b) * 1e-3
+
+    iters = 2000 if not fp32 else 100000
+    f, t = once(iters)
+    iters = max(1, int(iters * seconds / max(t, 1e-6)))
+    best = 0.0
+    for _ in range(repeats):
+        f, t = once(iters)
+        best = max(best, f / t / 1e12)
+    return best
 
 
 def integrate_noalloc(net: Network, y, T, dt: float, opts: Options, out, rho=None, stream=None):
