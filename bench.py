@@ -166,7 +166,7 @@ class ClockSampler:
 # ------------------------------------------------------------------ CPU oracle legs
 
 
-def oracle_time(wl: I.Workload, ncells: int, seed_offset: int = 0):
+def oracle_time(wl: I.Workload, ncells: int, seed_offset: int = 0, scheme: int = 1):
     """Time the FP64 oracle (as it stands) on the first ``ncells`` cells of a fresh
     draw of the workload; returns (cells/s, threads, wall seconds)."""
     from oracle import oracle
@@ -174,7 +174,7 @@ def oracle_time(wl: I.Workload, ncells: int, seed_offset: int = 0):
     net = oracle.OracleNetwork(wl.network)
     threads = os.cpu_count() or 1
     t0 = time.perf_counter()
-    r = net.integrate(sub, wl.tol.dt, oracle.options(wl.tol), threads)
+    r = net.integrate(sub, wl.tol.dt, oracle.options(wl.tol, scheme=scheme), threads)
     wall = time.perf_counter() - t0
     assert np.all(r["status"] <= 1)
     return ncells / wall, threads, wall
@@ -190,14 +190,17 @@ def hbm_peak_gbs() -> tuple:
         return 6800.0, "fallback (one earlier GB300 measurement)"
 
 
-def oracle_on(network: I.Network, cells: I.Cells, tol: I.Tolerances):
+SCHEME_NAMES = {0: "be_step_doubling", 1: "trbdf2"}
+
+
+def oracle_on(network: I.Network, cells: I.Cells, tol: I.Tolerances, scheme: int = 0):
     """The FP64 oracle (as it stands) on these cells with all host cores; returns
     (result dict, threads, wall seconds)."""
     from oracle import oracle
     net = oracle.OracleNetwork(network)
     threads = os.cpu_count() or 1
     t0 = time.perf_counter()
-    r = net.integrate(cells, tol.dt, oracle.options(tol), threads)
+    r = net.integrate(cells, tol.dt, oracle.options(tol, scheme=scheme), threads)
     return r, threads, time.perf_counter() - t0
 
 
@@ -245,8 +248,9 @@ def reference_arm(args):
             "config": dict(config_of(args, wl, args.ncells or I.FULL_CELLS[args.workload]),
                            timed_cells_per_step=n),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "scheme": SCHEME_NAMES[1],
                              "sample": f"{n} cells of the {wl.name} workload per step (same "
-                                       f"network, tolerances and dt), pthreads over cells"},
+                                       f"network, tolerances, dt and scheme), pthreads over cells"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -259,6 +263,8 @@ def config_of(args, wl: I.Workload, ncells: int) -> dict:
                         f"{' + temperature' if wl.network.energy else ''}, {ncells} cells, "
                         f"dt={t.dt:g} s, rtol={t.rtol:g}, atol={t.atol:g}",
             "ncells": ncells, "dt": t.dt, "rtol": t.rtol, "atol": t.atol,
+            "scheme": "TR-BDF2 sub-steps (the chosen form and the reference arm); "
+                      "the plain form is also timed with backward-Euler step doubling",
             "l2": "flushed between timed steps (256 MiB write)",
             "parallelism": f"cells sharded over {args.gpus} GPU(s), no collective"}
 
@@ -269,12 +275,12 @@ def config_of(args, wl: I.Workload, ncells: int) -> dict:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", type=int, default=2)
     ap.add_argument("--ncells", type=int, default=None)
-    ap.add_argument("--forms", default="plain,chosen")
+    ap.add_argument("--forms", default="plain,plain_trbdf2,chosen")
     ap.add_argument("--plain-steps", type=int, default=1,
                     help="timed steps of the plain FP64 form (context line, not the headline)")
     ap.add_argument("--e2e-steps", type=int, default=1)
@@ -284,7 +290,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-cells", type=int, default=1024)
-    ap.add_argument("--ref-cells", type=int, default=512)
+    ap.add_argument("--ref-cells", type=int, default=4096)
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -317,9 +323,10 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    forms = {"plain": dict(form=kt.KT_FORM_FP64, persistent=0),
-             "chosen": dict(form=kt.KT_FORM_FP32LU, persistent=1, guess=kt.KT_GUESS_FULLSTEP,
-                            use_graph=1, schedule=1)}
+    forms = {"plain": dict(form=kt.KT_FORM_FP64, persistent=0, scheme=kt.KT_SCHEME_BE),
+             "plain_trbdf2": dict(form=kt.KT_FORM_FP64, persistent=0, scheme=kt.KT_SCHEME_TRBDF2),
+             "chosen": dict(form=kt.KT_FORM_FP32LU, persistent=1, use_graph=1, schedule=1,
+                            scheme=kt.KT_SCHEME_TRBDF2)}
     tuned = None
     if not args.no_tune:
         base = kt.options(wl.tol, **forms["chosen"])
@@ -487,10 +494,17 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nsample = min(args.cpu_cells, ncells)
         sample = wl.cells.subset(range(nsample))
-        ora, threads, wall = oracle_on(wl.network, sample, wl.tol)
+        ora = {}
+        for scheme in sorted({int(forms[name].get("scheme", 0)) for name in results}):
+            ora[scheme] = oracle_on(wl.network, sample, wl.tol, scheme=scheme)
+        head_scheme = int(forms[head_name].get("scheme", 0))
+        _, threads, wall = ora[head_scheme]
         cpu = {"value": nsample / wall, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "scheme": SCHEME_NAMES[head_scheme],
                "sample": f"first {nsample} cells of the benchmark batch ({wl.name}, dt={wl.tol.dt:g} s), "
                          f"{wall:.1f} s wall"}
+        for scheme, (_, thr, w) in ora.items():
+            cpu[f"value_{SCHEME_NAMES[scheme]}"] = nsample / w
         for name in results:
             try:
                 so = kt.options(wl.tol, **forms[name])
@@ -498,7 +512,8 @@ def main():
                                  wl.tol.dt, so, rho=torch.from_numpy(sample.rho).to(dev))
                 kt.check_scratch(r["scratch"])
                 g = {k: r[k].cpu().numpy() for k in ("y", "T", "status", "nsub")}
-                results[name]["accuracy_vs_oracle"] = accuracy(g, ora, wl.network, sample.y)
+                results[name]["accuracy_vs_oracle"] = accuracy(
+                    g, ora[int(forms[name].get("scheme", 0))][0], wl.network, sample.y)
             except Exception as ex:          # a report, never a reason to lose the line
                 results[name]["accuracy_vs_oracle"] = {"error": repr(ex)[:300]}
 

@@ -64,6 +64,20 @@ extern "C" {
 #define KT_GUESS_FULLSTEP 2 /* second half step starts from the full step's result
                                (same end time; differs by the local error only) */
 
+/* one-step scheme of the sub-steps (the paper names a semi-implicit solver with
+ * adaptive sub-steps, Sec. 2.2, without fixing it) */
+#define KT_SCHEME_BE 0      /* backward Euler; error by step doubling (one step h vs two
+                               of h/2, the two-half-step result kept); first order */
+#define KT_SCHEME_TRBDF2 1  /* TR-BDF2 (Bank et al. 1985): a trapezoidal stage to
+                               t + gamma h and a BDF2 stage to t + h, gamma = 2 - sqrt(2),
+                               both solving y = r + d h f(y), d = gamma/2, with one
+                               iteration matrix I - d h J per step; error estimated from
+                               f at the three points, 2 C h (f_n/gamma - f_g/(gamma(1-gamma))
+                               + f_{n+1}/(1-gamma)), C = (-3 gamma^2 + 4 gamma - 2)/(12(2-gamma));
+                               h_new = h min(facmax, max(0.2, 0.9 err^(-1/3))); second
+                               order.  The second stage starts from the first stage's
+                               result whatever `guess` says; KT_GUESS_MLP is refused. */
+
 typedef struct kt_network kt_network;
 typedef struct kt_state kt_state;
 typedef struct kt_mlp kt_mlp;
@@ -106,7 +120,8 @@ typedef struct {
                                 previous call first (the state's n_newton counters;
                                 zero after kt_state_create), 0 in index order.  The
                                 order changes no result, only the load balance (0) */
-    int reserved[4];
+    int scheme;              /* KT_SCHEME_*: the one-step scheme of each sub-step      (BE) */
+    int reserved[3];
 } kt_options;
 
 /* Defaults listed above. */
@@ -116,8 +131,18 @@ KT_API int kt_options_default(kt_options *opts);
  * input generators ("kratos_network 1" header, species with molar mass, heat of
  * formation, heat capacity and element counts, reactions with up to three reactants
  * and products and modified-Arrhenius A, b, theta: k = A (T/t_ref)^b exp(-theta/T),
- * Sec. 2.2.1).  Every reaction must conserve every element (Eq. method-const-elem),
- * else KT_ENETWORK.  The caller owns *out and frees it with kt_network_free. */
+ * Sec. 2.2.1).  Optional sections before "end":
+ *   cv_poly t_mid, then "cvp s a0..a4 b0..b4" per species: heat capacities
+ *     cv_s(T) = sum_k a_k T^k below t_mid, sum_k b_k T^k above [J/(mol K)] (Sec. 4.2,
+ *     NASA-style fits); C_V(T) = sum_s n0_s cv_s(T) with the cell's input composition;
+ *   photo m, then "ph r sigma_r" m times: one-reactant photo-reactions (see
+ *     kt_integrate_rad);
+ *   rate_table nT T0 T1 nR rho0 rho1 m, then "tab r" and nR x nT values of ln k m times:
+ *     tabulated rates (Sec. 2.2.1 item 3) on log-spaced nodes; each cell takes ln k
+ *     linear in ln rho at its density (pre-processing, Sec. 2.2.2), then ln k linear in
+ *     ln T between nodes (dk/dT from that slope), constant beyond the grid.
+ * Every reaction must conserve every element (Eq. method-const-elem), else
+ * KT_ENETWORK.  The caller owns *out and frees it with kt_network_free. */
 KT_API int kt_network_load(const char *path, kt_network **out);
 
 /* Sizes of a loaded network.  Any output pointer may be NULL. */
@@ -189,6 +214,22 @@ KT_API int kt_autotune(const kt_network *net, int64_t ncells, const double *y_in
                        const double *T_in, double dt, const kt_options *base,
                        double *y_out, double *T_out, void *scratch, void *cuda_stream,
                        kt_options *best, double *best_seconds);
+
+/* kt_integrate_ptrs for networks with photo-reactions (Sec. 2.2.1 item 2, Eq.
+ * photo-reaction-single): per cell the photo flux factor flux[c] = L dl / dV
+ * [photons cm^-2 s^-1 per unit cross-section] and the path length path[c] = dl [cm]
+ * (device float64 [ncells]; either may be NULL: flux 1, path 0).  A photo-reaction of
+ * reactant i with cross-section sigma_r runs at k = flux sigma_r (1 - e^-tau)/tau,
+ * tau = path sum_s n_s sigma_s over every absorbing species (the optically thin limit
+ * flux sigma_r when path = 0), with the exact Jacobian of tau's dependence on every
+ * absorber.  rho (may be NULL: 1) also selects the cell's slice of the network's rate
+ * tables.  Same buffer rules as kt_integrate_ptrs.  Networks with tabulated or photo
+ * rates run in the warp-per-cell kernels (cells_per_warp 0 or 1). */
+KT_API int kt_integrate_rad(const kt_network *net, int64_t ncells, const double *y_in,
+                            const double *T_in, const double *rho, const double *flux,
+                            const double *path, double dt, const kt_options *opts, double *y_out,
+                            double *T_out, int32_t *status, int32_t *n_substeps, int32_t *n_newton,
+                            void *scratch, void *cuda_stream);
 
 /* kt_integrate_ptrs with a per-cell time step: dt_cells [ncells] (device, float64,
  * each > 0; a cell whose dt is not a positive finite number gets status

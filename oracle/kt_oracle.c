@@ -14,6 +14,8 @@
  *
  * What is computed (each function cites the passage it follows):
  *   ko_rates       modified Arrhenius k(T) and dk/dT          Sec. 2.2.1 item 1
+ *   cell_rates     + tabulated (reduced per cell) and photo    Sec. 2.2.1 items 2-3, Sec. 2.2.2,
+ *                  rates k = F sigma (1 - e^-tau)/tau           Eq. photo-reaction-single
  *   ko_rhs         dn/dt = sum A n n + sum B n,  dT/dt        Eq. method-ode-thermochem
  *   ko_jacobian    mass-action + thermal-coupling partials    Eq. method-jacobian, Sec. 2.2.1
  *   ko_lu          Crout LU, implicit-scaled row pivoting     Algorithm lu-decomp, Sec. 2.3.2
@@ -50,6 +52,8 @@
 #define KO_MAXN 80      /* unknowns per cell (species + T) */
 #define KO_MAXE 8       /* elements */
 #define KO_MAXSIDE 3    /* reactants / products per reaction */
+#define KO_MAXTAB 64    /* tabulated reactions per network */
+#define KO_MAXTN 64     /* temperature / density nodes of a rate table */
 
 #define KO_OK 0
 #define KO_EINVAL (-1)
@@ -71,7 +75,30 @@ typedef struct {
     int *nin, *nout;            /* [nr] */
     int *in, *out;              /* [nr*KO_MAXSIDE] */
     double *A, *b, *theta;      /* [nr] */
+    /* rate types (Sec. 2.2.1): 0 modified Arrhenius, 1 tabulated, 2 photo-reaction */
+    int *rtype;                 /* [nr] */
+    double *sig_r;              /* [nr]: photo cross-section of a type-2 reaction [cm^2] */
+    double *sig_s;              /* [ns]: absorption cross-section of each species, the sum
+                                   of its photo reactions' [cm^2] */
+    int ntab, tab_nT, tab_nR;   /* tabulated reactions and their grid */
+    double tab_T0, tab_T1, tab_R0, tab_R1;   /* log-spaced T and rho nodes, end points */
+    int *tab_of;                /* [nr]: table row of a type-1 reaction, -1 otherwise */
+    double *tab;                /* [ntab][nR][nT]: ln k at the nodes */
+    int cvpoly;                 /* 1: heat capacities are two-range polynomials in T */
+    double t_mid;               /* boundary of the two ranges [K] */
+    double *cvp;                /* [ns*10]: cv_s(T) = sum_k cvp[10s+k] T^k below t_mid,
+                                   sum_k cvp[10s+5+k] T^k from t_mid, J/(mol K) */
 } ko_net;
+
+/* Heat capacity per volume of one cell, C_V = sum_s cv_s n_s with the composition n0
+ * frozen at the cell's pre-processed input (operator split; the paper's Jacobian
+ * neglects dC_V/dn as well).  Constant networks: C_V = cv0.  Polynomial networks
+ * (Sec. 4.2, NASA-style fits): C_V(T) = sum_s n0_s cv_s(T); with n0 NULL the constant
+ * cv0 is used (single-step pins). */
+typedef struct {
+    double cv0;
+    const double *n0;
+} ko_heat;
 
 typedef struct {
     double rtol, atol, h_init, h_min;
@@ -139,7 +166,8 @@ void ko_free(ko_net *n)
     if (!n) return;
     free(n->mass); free(n->h); free(n->cv); free(n->counts);
     free(n->nin); free(n->nout); free(n->in); free(n->out);
-    free(n->A); free(n->b); free(n->theta);
+    free(n->A); free(n->b); free(n->theta); free(n->cvp);
+    free(n->rtype); free(n->sig_r); free(n->sig_s); free(n->tab_of); free(n->tab);
     free(n);
 }
 
@@ -200,7 +228,64 @@ int ko_load(const char *path, ko_net **out)
         ok = ok && read_dbl(f, &n->A[i]) && read_dbl(f, &n->b[i]) &&
              read_dbl(f, &n->theta[i]) && read_int(f, &pair);
     }
-    ok = ok && expect(f, "end");
+    /* optional sections (heat capacities, photo-reactions, rate tables), then "end" */
+    n->rtype = calloc(n->nr + 1, sizeof(int));
+    n->sig_r = calloc(n->nr + 1, sizeof(double));
+    n->sig_s = calloc(n->ns, sizeof(double));
+    n->tab_of = malloc((n->nr + 1) * sizeof(int));
+    if (!n->rtype || !n->sig_r || !n->sig_s || !n->tab_of) ok = 0;
+    for (i = 0; ok && i < n->nr; i++) n->tab_of[i] = -1;
+    while (ok) {
+        ok = next_token(f, buf, sizeof buf);
+        if (!ok || strcmp(buf, "end") == 0) break;
+        if (strcmp(buf, "cv_poly") == 0 && !n->cvpoly) {
+            n->cvpoly = 1;
+            n->cvp = calloc((size_t)n->ns * 10, sizeof(double));
+            ok = n->cvp != NULL && n->energy == 1 && read_dbl(f, &n->t_mid) && n->t_mid > 0.0;
+            for (i = 0; i < n->ns && ok; i++) {
+                int sp;
+                ok = expect(f, "cvp") && read_int(f, &sp) && sp == i;
+                for (j = 0; j < 10 && ok; j++) ok = read_dbl(f, &n->cvp[i * 10 + j]);
+            }
+        } else if (strcmp(buf, "photo") == 0) {
+            /* photo <count>, then "ph <reaction> <cross-section>" (one reactant each) */
+            int np;
+            ok = read_int(f, &np) && np >= 0 && np <= n->nr;
+            for (i = 0; i < np && ok; i++) {
+                int r;
+                double sg;
+                ok = expect(f, "ph") && read_int(f, &r) && r >= 0 && r < n->nr && read_dbl(f, &sg) &&
+                     sg >= 0.0 && n->nin[r] == 1 && n->rtype[r] == 0;
+                if (ok) {
+                    n->rtype[r] = 2;
+                    n->sig_r[r] = sg;
+                    n->sig_s[n->in[r * KO_MAXSIDE]] += sg;
+                }
+            }
+        } else if (strcmp(buf, "rate_table") == 0 && !n->tab) {
+            /* rate_table <nT> <T0> <T1> <nR> <rho0> <rho1> <count>, then per reaction
+             * "tab <reaction>" and nR x nT values of ln k (rho-major) */
+            ok = read_int(f, &n->tab_nT) && read_dbl(f, &n->tab_T0) && read_dbl(f, &n->tab_T1) &&
+                 read_int(f, &n->tab_nR) && read_dbl(f, &n->tab_R0) && read_dbl(f, &n->tab_R1) &&
+                 read_int(f, &n->ntab) && n->tab_nT >= 2 && n->tab_nT <= KO_MAXTN && n->tab_nR >= 1 &&
+                 n->tab_nR <= KO_MAXTN && n->ntab >= 0 && n->ntab <= KO_MAXTAB && n->ntab <= n->nr &&
+                 n->tab_T0 > 0.0 && n->tab_T1 > n->tab_T0 && n->tab_R0 > 0.0 &&
+                 (n->tab_nR == 1 || n->tab_R1 > n->tab_R0);
+            if (ok) n->tab = calloc((size_t)(n->ntab + 1) * n->tab_nR * n->tab_nT, sizeof(double));
+            ok = ok && n->tab != NULL;
+            for (i = 0; i < n->ntab && ok; i++) {
+                int r, q, m = n->tab_nR * n->tab_nT;
+                ok = expect(f, "tab") && read_int(f, &r) && r >= 0 && r < n->nr && n->rtype[r] == 0;
+                if (ok) {
+                    n->rtype[r] = 1;
+                    n->tab_of[r] = i;
+                }
+                for (q = 0; q < m && ok; q++) ok = read_dbl(f, &n->tab[(size_t)i * m + q]);
+            }
+        } else {
+            ok = 0;
+        }
+    }
     fclose(f);
     if (!ok) { ko_free(n); return KO_EPARSE; }
     /* every reaction must conserve every element (Eq. method-const-elem) */
@@ -245,11 +330,141 @@ int ko_rates(const ko_net *n, double T, double *k, double *dkdT)
     return KO_OK;
 }
 
+/* C_V of the cell at temperature T and its derivative dC_V/dT (see ko_heat). */
+static double heat_capacity(const ko_net *n, const ko_heat *hc, double T, double *dcv)
+{
+    int s, k;
+    if (!n->cvpoly || !hc->n0) {
+        *dcv = 0.0;
+        return hc->cv0;
+    }
+    double c = 0.0, d = 0.0;
+    for (s = 0; s < n->ns; s++) {
+        const double *a = n->cvp + s * 10 + (T < n->t_mid ? 0 : 5);
+        double v = 0.0, dv = 0.0, tk = 1.0;
+        for (k = 0; k < 5; k++) {
+            v += a[k] * tk;
+            if (k < 4) dv += (k + 1) * a[k + 1] * tk;
+            tk *= T;
+        }
+        c += hc->n0[s] * v;
+        d += hc->n0[s] * dv;
+    }
+    *dcv = d;
+    return c;
+}
+
+/* Per-cell radiation and table data: the photo flux factor F = L dl / dV and path
+ * length dl of Eq. photo-reaction-single, and the cell's rate tables reduced to one
+ * dimension in T at its density (Sec. 2.2.2, "rate table generation"). */
+typedef struct {
+    double flux, path;
+    const double *ltab;         /* [ntab][nT] ln k at the T nodes */
+} ko_rad;
+
+/* Pre-processing of the tables: ln k at the T nodes for density rho, linear in ln rho
+ * between the two bracketing density nodes (clamped to the grid). */
+static void table_reduce(const ko_net *n, double rho, double *ltab)
+{
+    int t, j, nT = n->tab_nT, nR = n->tab_nR;
+    double u = 0.0, w = 0.0;
+    int i = 0;
+    if (nR > 1) {
+        u = (log(rho) - log(n->tab_R0)) / (log(n->tab_R1) - log(n->tab_R0)) * (nR - 1);
+        if (!(u > 0.0)) u = 0.0;
+        if (u > nR - 1) u = nR - 1;
+        i = (int)floor(u);
+        if (i > nR - 2) i = nR - 2;
+        w = u - i;
+    }
+    for (t = 0; t < n->ntab; t++)
+        for (j = 0; j < nT; j++) {
+            const double *row = n->tab + ((size_t)t * nR + i) * nT;
+            ltab[t * nT + j] = nR > 1 ? (1.0 - w) * row[j] + w * row[nT + j] : row[j];
+        }
+}
+
+/* k and dk/dT of tabulated reaction t at T: ln k linear in ln T between the nodes
+ * (so dk/dT = k (ln k_{j+1} - ln k_j) / (d ln T) / T), constant beyond the grid. */
+static void table_eval(const ko_net *n, const double *ltab, int t, double T, double *k, double *dk)
+{
+    const double *L = ltab + t * n->tab_nT;
+    int nT = n->tab_nT;
+    double dl = (log(n->tab_T1) - log(n->tab_T0)) / (nT - 1);
+    double v = (log(T) - log(n->tab_T0)) / dl;
+    if (!(v > 0.0)) { *k = exp(L[0]); *dk = 0.0; return; }
+    if (v >= nT - 1) { *k = exp(L[nT - 1]); *dk = 0.0; return; }
+    int j = (int)floor(v);
+    if (j > nT - 2) j = nT - 2;
+    double fr = v - j;
+    *k = exp(L[j] + fr * (L[j + 1] - L[j]));
+    *dk = *k * ((L[j + 1] - L[j]) / dl) / T;
+}
+
+/* phi(tau) = (1 - exp(-tau)) / tau (Eq. photo-reaction-single) and its derivative;
+ * below tau = 0.1 by their Taylor series (8 terms), where the closed forms cancel. */
+static void photo_phi(double tau, double *phi, double *dphi)
+{
+    if (tau < 0.1) {
+        /* phi = sum_k (-tau)^k / (k+1)!,  phi' = sum_{k>=1} (-1)^k k tau^(k-1) / (k+1)! */
+        double p = 0.0, d = 0.0, pw = 1.0, pwm = 0.0, fact = 1.0;
+        int k;
+        for (k = 0; k < 9; k++) {
+            fact *= (k + 1);
+            double sg = (k & 1) ? -1.0 : 1.0;
+            p += sg * pw / fact;
+            if (k >= 1) d += sg * k * pwm / fact;
+            pwm = pw;
+            pw *= tau;
+        }
+        *phi = p;
+        *dphi = d;
+    } else {
+        double e = exp(-tau);
+        *phi = (1.0 - e) / tau;
+        *dphi = (e * (1.0 + tau) - 1.0) / (tau * tau);
+    }
+}
+
+/* Optical depth of the cell, tau = dl sum_s n_s sigma_s. */
+static double optical_depth(const ko_net *n, const ko_rad *rd, const double *y)
+{
+    double s = 0.0;
+    int i;
+    for (i = 0; i < n->ns; i++) s += y[i] * n->sig_s[i];
+    return rd->path * s;
+}
+
+/* Rate coefficients of one cell at state y and temperature T: modified Arrhenius,
+ * tabulated (the cell's reduced tables) and photo-reactions k_r = F sigma_r phi(tau)
+ * (Sec. 2.2.1 items 1-3; dk/dT = 0 for the latter). */
+static int cell_rates(const ko_net *n, const ko_rad *rd, const double *y, double T, double *k, double *dk)
+{
+    int r, rc = ko_rates(n, T, k, dk);
+    if (rc) return rc;
+    if (!n->rtype) return KO_OK;
+    double phi = 1.0, dphi = 0.0;
+    int have_phi = 0;
+    for (r = 0; r < n->nr; r++) {
+        if (n->rtype[r] == 1) {
+            table_eval(n, rd->ltab, n->tab_of[r], T, &k[r], &dk[r]);
+        } else if (n->rtype[r] == 2) {
+            if (!have_phi) {
+                photo_phi(optical_depth(n, rd, y), &phi, &dphi);
+                have_phi = 1;
+            }
+            k[r] = rd->flux * n->sig_r[r] * phi;
+            dk[r] = 0.0;
+        }
+    }
+    return KO_OK;
+}
+
 /* Right-hand side (Eq. method-ode-thermochem): each reaction's rate is
  * w_r = k_r * prod(reactant densities); every reactant occurrence loses w_r and
  * every product occurrence gains w_r.  With the energy equation the last unknown is
- * T and dT/dt = -sum_s h_s dn_s/dt / C_V. */
-static void rhs(const ko_net *n, const double *y, const double *k, double cvtot, double *f)
+ * T and dT/dt = -sum_s h_s dn_s/dt / C_V(T). */
+static void rhs(const ko_net *n, const double *y, const double *k, const ko_heat *hc, double *f)
 {
     int N = n->ns + n->energy, r, j;
     for (j = 0; j < N; j++) f[j] = 0.0;
@@ -262,14 +477,16 @@ static void rhs(const ko_net *n, const double *y, const double *k, double cvtot,
     if (n->energy) {
         double q = 0.0;
         for (j = 0; j < n->ns; j++) q += n->h[j] * f[j];
-        f[n->ns] = -q / cvtot;
+        double dcv;
+        f[n->ns] = -q / heat_capacity(n, hc, y[n->ns], &dcv);
     }
 }
 
 /* Analytic Jacobian (Eq. method-jacobian and the mass-action derivative cases;
- * thermal coupling through dk/dT, with dC_V/dn neglected as the paper does). */
+ * thermal coupling through dk/dT, with dC_V/dn neglected as the paper does).  With
+ * C_V(T) the temperature row's T entry also carries -f_T C_V'(T) / C_V(T). */
 static void jacobian(const ko_net *n, const double *y, const double *k, const double *dkdT,
-                     double cvtot, double *J)
+                     const ko_heat *hc, const ko_rad *rd, double *J)
 {
     int N = n->ns + n->energy, r, j, l, a;
     for (j = 0; j < N * N; j++) J[j] = 0.0;
@@ -290,34 +507,91 @@ static void jacobian(const ko_net *n, const double *y, const double *k, const do
             for (a = 0; a < n->nin[r]; a++) J[in[a] * N + n->ns] -= dT;
             for (a = 0; a < n->nout[r]; a++) J[out[a] * N + n->ns] += dT;
         }
+        if (n->rtype && n->rtype[r] == 2 && rd->path > 0.0) {
+            /* photo rate w = F sigma_r phi(tau) n_i with tau = dl sum_m n_m sigma_m:
+             * dw/dn_m also carries F sigma_r n_i phi'(tau) dl sigma_m (every absorber) */
+            double phi, dphi;
+            photo_phi(optical_depth(n, rd, y), &phi, &dphi);
+            double g = rd->flux * n->sig_r[r] * y[in[0]] * dphi * rd->path;
+            int m;
+            for (m = 0; m < n->ns; m++) {
+                double d = g * n->sig_s[m];
+                if (d == 0.0) continue;
+                J[in[0] * N + m] -= d;
+                for (a = 0; a < n->nout[r]; a++) J[out[a] * N + m] += d;
+            }
+        }
     }
     if (n->energy) {
         int m;
+        double dcv, cv = heat_capacity(n, hc, y[n->ns], &dcv);
         for (m = 0; m < N; m++) {
             double q = 0.0;
             for (j = 0; j < n->ns; j++) q += n->h[j] * J[j * N + m];
-            J[n->ns * N + m] = -q / cvtot;
+            J[n->ns * N + m] = -q / cv;
+        }
+        if (dcv != 0.0) {
+            double f[KO_MAXN];
+            rhs(n, y, k, hc, f);
+            J[n->ns * N + n->ns] -= f[n->ns] * dcv / cv;
         }
     }
 }
 
-int ko_rhs(const ko_net *n, const double *y, double T_iso, double cvtot, double *f)
+/* Parameters of one cell for the pins: the isothermal temperature, C_V (constant, or
+ * the frozen composition n0 of C_V(T)), the density (rate tables) and the photo flux
+ * factor and path length (photo-reactions). */
+typedef struct {
+    double T_iso, cvtot;
+    const double *n0;
+    double rho, flux, path;
+} ko_cellpar;
+
+static void par_setup(const ko_net *n, const ko_cellpar *p, ko_heat *hc, ko_rad *rd, double *ltab)
 {
+    hc->cv0 = p->cvtot;
+    hc->n0 = p->n0;
+    rd->flux = p->flux;
+    rd->path = p->path;
+    rd->ltab = ltab;
+    if (n->ntab) table_reduce(n, p->rho, ltab);
+}
+
+/* Rate coefficients, f(y) and J(y) of one state (pins). */
+int ko_rates_cell(const ko_net *n, const double *y, const ko_cellpar *p, double *k, double *dk)
+{
+    double ltab[KO_MAXTAB * KO_MAXTN];
+    ko_heat hc;
+    ko_rad rd;
+    par_setup(n, p, &hc, &rd, ltab);
+    return cell_rates(n, &rd, y, n->energy ? y[n->ns] : p->T_iso, k, dk);
+}
+
+int ko_rhs(const ko_net *n, const double *y, const ko_cellpar *p, double *f)
+{
+    double ltab[KO_MAXTAB * KO_MAXTN];
     double k[4096], dk[4096];
+    ko_heat hc;
+    ko_rad rd;
     if (n->nr > 4096) return KO_EINVAL;
-    int rc = ko_rates(n, n->energy ? y[n->ns] : T_iso, k, dk);
+    par_setup(n, p, &hc, &rd, ltab);
+    int rc = cell_rates(n, &rd, y, n->energy ? y[n->ns] : p->T_iso, k, dk);
     if (rc) return rc;
-    rhs(n, y, k, cvtot, f);
+    rhs(n, y, k, &hc, f);
     return KO_OK;
 }
 
-int ko_jacobian(const ko_net *n, const double *y, double T_iso, double cvtot, double *J)
+int ko_jacobian(const ko_net *n, const double *y, const ko_cellpar *p, double *J)
 {
+    double ltab[KO_MAXTAB * KO_MAXTN];
     double k[4096], dk[4096];
+    ko_heat hc;
+    ko_rad rd;
     if (n->nr > 4096) return KO_EINVAL;
-    int rc = ko_rates(n, n->energy ? y[n->ns] : T_iso, k, dk);
+    par_setup(n, p, &hc, &rd, ltab);
+    int rc = cell_rates(n, &rd, y, n->energy ? y[n->ns] : p->T_iso, k, dk);
     if (rc) return rc;
-    jacobian(n, y, k, dk, cvtot, J);
+    jacobian(n, y, k, dk, &hc, &rd, J);
     return KO_OK;
 }
 
@@ -395,6 +669,10 @@ typedef struct {
     const ko_options *o;
     int N;
     double T_iso, cvtot;
+    double n0[KO_MAXN];       /* pre-processed composition (C_V(T) of polynomial networks) */
+    ko_heat hc;
+    ko_rad rd;                /* photo flux factor and path length, reduced rate tables */
+    double ltab[KO_MAXTAB * KO_MAXTN];
     double atol_s;            /* species absolute tolerance for this cell */
     double k[4096], dk[4096];
     double f[KO_MAXN], G[KO_MAXN], d[KO_MAXN];
@@ -425,10 +703,10 @@ static int be_solve(ko_cell *c, const double *yn, double h, double *y)
         c->nnewton++;
         double T = n->energy ? y[n->ns] : c->T_iso;
         if (!(T > 0.0)) return -1;
-        ko_rates(n, T, c->k, c->dk);
-        rhs(n, y, c->k, c->cvtot, c->f);
+        cell_rates(n, &c->rd, y, T, c->k, c->dk);
+        rhs(n, y, c->k, &c->hc, c->f);
         for (i = 0; i < N; i++) c->G[i] = y[i] - yn[i] - h * c->f[i];
-        jacobian(n, y, c->k, c->dk, c->cvtot, c->J);
+        jacobian(n, y, c->k, c->dk, &c->hc, &c->rd, c->J);
         for (i = 0; i < N; i++)
             for (j = 0; j < N; j++)
                 c->M[i * N + j] = (i == j ? 1.0 : 0.0) - h * c->J[i * N + j];
@@ -503,8 +781,8 @@ static int trbdf2_step(ko_cell *c, const double *yn, double h, double *y1, doubl
     double f0[KO_MAXN], r[KO_MAXN], yg[KO_MAXN];
     double T = n->energy ? yn[n->ns] : c->T_iso;
     if (!(T > 0.0)) return -1;
-    ko_rates(n, T, c->k, c->dk);
-    rhs(n, yn, c->k, c->cvtot, f0);
+    cell_rates(n, &c->rd, yn, T, c->k, c->dk);
+    rhs(n, yn, c->k, &c->hc, f0);
     const double dh = k.d * h, inv = 1.0 / dh;
     for (i = 0; i < N; i++) r[i] = yn[i] + dh * f0[i];
     for (i = 0; i < N; i++) yg[i] = yn[i];
@@ -702,7 +980,8 @@ static int post_process(const ko_cell *c, double *y, const double *b0)
 
 /* One cell: pre-process, integrate, post-process, retry / revert (Sec. 2.2.2-2.2.3). */
 static void integrate_cell(const ko_net *n, const ko_options *o, double dt,
-                           const double *yin, double Tin, double *yout, double *Tout,
+                           const double *yin, double Tin, double rho, double flux, double path,
+                           double *yout, double *Tout,
                            int32_t *status, int32_t *nsub, int32_t *nnew, ko_cell *c)
 {
     int ns = n->ns, N = ns + n->energy, s, e;
@@ -710,6 +989,11 @@ static void integrate_cell(const ko_net *n, const ko_options *o, double dt,
     int finite = isfinite(Tin);
     for (s = 0; s < ns; s++) finite = finite && isfinite(yin[s]);
     c->n = n; c->o = o; c->N = N; c->nnewton = 0;
+    /* pre-processing (Sec. 2.2.2): the cell's rate tables at its density */
+    c->rd.flux = flux;
+    c->rd.path = path;
+    c->rd.ltab = c->ltab;
+    if (n->ntab) table_reduce(n, rho, c->ltab);
     if (!finite) {
         for (s = 0; s < ns; s++) yout[s] = yin[s];
         *Tout = Tin; *status = KO_ST_NONFINITE; *nsub = 0; *nnew = 0;
@@ -727,6 +1011,9 @@ static void integrate_cell(const ko_net *n, const ko_options *o, double dt,
     }
     c->cvtot = 0.0;
     for (s = 0; s < ns; s++) c->cvtot += n->cv[s] * y0[s];
+    for (s = 0; s < ns; s++) c->n0[s] = y0[s];
+    c->hc.cv0 = c->cvtot;
+    c->hc.n0 = c->n0;
     c->atol_s = o->atol;
     if (o->atol_mode == 1 && b0[0] > 0.0) c->atol_s = o->atol * b0[0];
 
@@ -757,7 +1044,7 @@ typedef struct {
     const ko_options *o;
     double dt;
     int64_t ncells;
-    const double *y, *T;
+    const double *y, *T, *rho, *flux, *path;
     double *yo, *To;
     int32_t *st, *nsub, *nnew;
     int64_t next;
@@ -778,8 +1065,9 @@ static void *worker(void *arg)
         if (i >= jb->ncells) break;
         for (s = 0; s < ns; s++) yin[s] = jb->y[(int64_t)s * jb->ncells + i];
         double To;
-        integrate_cell(jb->n, jb->o, jb->dt, yin, jb->T[i], yout, &To, &jb->st[i],
-                       &jb->nsub[i], &jb->nnew[i], c);
+        integrate_cell(jb->n, jb->o, jb->dt, yin, jb->T[i], jb->rho ? jb->rho[i] : 1.0,
+                       jb->flux ? jb->flux[i] : 1.0, jb->path ? jb->path[i] : 0.0, yout, &To,
+                       &jb->st[i], &jb->nsub[i], &jb->nnew[i], c);
         for (s = 0; s < ns; s++) jb->yo[(int64_t)s * jb->ncells + i] = yout[s];
         jb->To[i] = To;
     }
@@ -788,19 +1076,21 @@ static void *worker(void *arg)
 }
 
 /* Integrate ncells cells over dt.  y, y_out: [ns][ncells] SoA; T, T_out: [ncells].
- * rho is accepted for interface symmetry and unused by the ODE.  nthreads <= 0 means 1. */
-int ko_integrate(const ko_net *n, int64_t ncells, const double *y, const double *T,
-                 const double *rho, double dt, const ko_options *o, int nthreads,
-                 double *y_out, double *T_out, int32_t *status, int32_t *nsub, int32_t *nnew)
+ * rho (rate tables; NULL: 1), flux and path (photo-reactions, Eq. photo-reaction-single;
+ * NULL: F = 1 and dl = 0, the optically thin limit k = sigma) are per cell.
+ * nthreads <= 0 means 1. */
+int ko_integrate_rad(const ko_net *n, int64_t ncells, const double *y, const double *T,
+                     const double *rho, const double *flux, const double *path, double dt,
+                     const ko_options *o, int nthreads, double *y_out, double *T_out,
+                     int32_t *status, int32_t *nsub, int32_t *nnew)
 {
-    (void)rho;
     if (!n || !o || ncells < 0 || !(dt > 0.0) || !(o->atol > 0.0) || !(o->rtol > 0.0) ||
         o->max_newton < 1 || o->max_substeps < 1 || !(o->h_init > 0.0))
         return KO_EINVAL;
     if (ncells == 0) return KO_OK;
     if (nthreads < 1) nthreads = 1;
     if (nthreads > 512) nthreads = 512;
-    ko_job jb = {n, o, dt, ncells, y, T, y_out, T_out, status, nsub, nnew, 0,
+    ko_job jb = {n, o, dt, ncells, y, T, rho, flux, path, y_out, T_out, status, nsub, nnew, 0,
                  PTHREAD_MUTEX_INITIALIZER};
     pthread_t th[512];
     int t, started = 0;
@@ -812,6 +1102,14 @@ int ko_integrate(const ko_net *n, int64_t ncells, const double *y, const double 
     return KO_OK;
 }
 
+int ko_integrate(const ko_net *n, int64_t ncells, const double *y, const double *T,
+                 const double *rho, double dt, const ko_options *o, int nthreads,
+                 double *y_out, double *T_out, int32_t *status, int32_t *nsub, int32_t *nnew)
+{
+    return ko_integrate_rad(n, ncells, y, T, rho, NULL, NULL, dt, o, nthreads, y_out, T_out, status,
+                            nsub, nnew);
+}
+
 /* One backward-Euler step of one cell (pins): y_out = root of y - yn - h f(y). */
 int ko_be_step(const ko_net *n, const ko_options *o, const double *yn, double T_iso,
                double cvtot, double h, double *y_out, int *n_iter)
@@ -820,6 +1118,9 @@ int ko_be_step(const ko_net *n, const ko_options *o, const double *yn, double T_
     int i, rc;
     if (!c) return KO_ENOMEM;
     c->n = n; c->o = o; c->N = n->ns + n->energy; c->T_iso = T_iso; c->cvtot = cvtot;
+    c->hc.cv0 = cvtot; c->hc.n0 = NULL;
+    c->rd.flux = 1.0; c->rd.path = 0.0; c->rd.ltab = c->ltab;
+    if (n->ntab) table_reduce(n, 1.0, c->ltab);
     c->atol_s = o->atol; c->nnewton = 0;
     for (i = 0; i < c->N; i++) y_out[i] = yn[i];
     rc = be_solve(c, yn, h, y_out);
@@ -852,6 +1153,9 @@ int ko_trbdf2_step(const ko_net *n, const ko_options *o, const double *yn, doubl
     int rc;
     if (!c) return KO_ENOMEM;
     c->n = n; c->o = o; c->N = n->ns + n->energy; c->T_iso = T_iso; c->cvtot = cvtot;
+    c->hc.cv0 = cvtot; c->hc.n0 = NULL;
+    c->rd.flux = 1.0; c->rd.path = 0.0; c->rd.ltab = c->ltab;
+    if (n->ntab) table_reduce(n, 1.0, c->ltab);
     c->atol_s = o->atol; c->nnewton = 0;
     rc = trbdf2_step(c, yn, h, y_out, est_out);
     free(c);

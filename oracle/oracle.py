@@ -45,6 +45,13 @@ class Options(ctypes.Structure):
                 ("atol_mode", ctypes.c_int), ("guess", ctypes.c_int), ("scheme", ctypes.c_int)]
 
 
+class CellPar(ctypes.Structure):
+    """Per-cell parameters of the single-state pins (ko_cellpar)."""
+    _fields_ = [("T_iso", ctypes.c_double), ("cvtot", ctypes.c_double),
+                ("n0", ctypes.POINTER(ctypes.c_double)), ("rho", ctypes.c_double),
+                ("flux", ctypes.c_double), ("path", ctypes.c_double)]
+
+
 def options(tol=None, **kw) -> Options:
     """Options from an ``inputs.Tolerances`` plus keyword overrides."""
     d = dict(rtol=1e-6, atol=1e-10, h_init=1e-6, h_min=1e-30, newton_rtol=1e-12,
@@ -71,14 +78,16 @@ def lib():
             L.ko_free.argtypes = [vp]
             L.ko_info.argtypes = [vp, ip, ip, ip, ip]
             L.ko_rates.argtypes = [vp, ctypes.c_double, dp, dp]
-            L.ko_rhs.argtypes = [vp, dp, ctypes.c_double, ctypes.c_double, dp]
-            L.ko_jacobian.argtypes = [vp, dp, ctypes.c_double, ctypes.c_double, dp]
+            cp = ctypes.POINTER(CellPar)
+            L.ko_rhs.argtypes = [vp, dp, cp, dp]
+            L.ko_jacobian.argtypes = [vp, dp, cp, dp]
+            L.ko_rates_cell.argtypes = [vp, dp, cp, dp, dp]
             L.ko_lu.argtypes = [ctypes.c_int, dp, ip]
             L.ko_lu_solve.argtypes = [ctypes.c_int, dp, ip, dp]
             L.ko_lu_solve.restype = None
-            L.ko_integrate.argtypes = [vp, ctypes.c_int64, dp, dp, dp, ctypes.c_double,
-                                       ctypes.POINTER(Options), ctypes.c_int, dp, dp,
-                                       i32p, i32p, i32p]
+            L.ko_integrate_rad.argtypes = [vp, ctypes.c_int64, dp, dp, dp, dp, dp, ctypes.c_double,
+                                           ctypes.POINTER(Options), ctypes.c_int, dp, dp,
+                                           i32p, i32p, i32p]
             L.ko_be_step.argtypes = [vp, ctypes.POINTER(Options), dp, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, dp, ip]
             L.ko_post_process.argtypes = [vp, dp, dp]
@@ -132,21 +141,47 @@ class OracleNetwork:
             raise ValueError("rates failed")
         return k[:self.nr], dk[:self.nr]
 
-    def rhs(self, y, T_iso: float = 300.0, cvtot: float = 1.0):
+    @staticmethod
+    def _par(T_iso, cvtot, n0, rho, flux, path):
+        n0 = None if n0 is None else np.ascontiguousarray(n0, float)
+        p = CellPar(float(T_iso), float(cvtot), None if n0 is None else _dp(n0), float(rho),
+                    float(flux), float(path))
+        return p, n0
+
+    def rhs(self, y, T_iso: float = 300.0, cvtot: float = 1.0, n0=None, rho: float = 1.0,
+            flux: float = 1.0, path: float = 0.0):
+        """f(y); cvtot is C_V of constant-heat-capacity networks, n0 the frozen
+        composition of C_V(T) on polynomial ones; rho reduces the rate tables; flux and
+        path are the photo-reaction parameters of the cell."""
         y = np.ascontiguousarray(y, float)
         f = np.zeros(self.n)
-        rc = lib().ko_rhs(self.ptr, _dp(y), float(T_iso), float(cvtot), _dp(f))
+        p, keep = self._par(T_iso, cvtot, n0, rho, flux, path)
+        rc = lib().ko_rhs(self.ptr, _dp(y), ctypes.byref(p), _dp(f))
         if rc:
             raise ValueError("rhs failed")
         return f
 
-    def jacobian(self, y, T_iso: float = 300.0, cvtot: float = 1.0):
+    def jacobian(self, y, T_iso: float = 300.0, cvtot: float = 1.0, n0=None, rho: float = 1.0,
+                 flux: float = 1.0, path: float = 0.0):
         y = np.ascontiguousarray(y, float)
         J = np.zeros((self.n, self.n))
-        rc = lib().ko_jacobian(self.ptr, _dp(y), float(T_iso), float(cvtot), _dp(J))
+        p, keep = self._par(T_iso, cvtot, n0, rho, flux, path)
+        rc = lib().ko_jacobian(self.ptr, _dp(y), ctypes.byref(p), _dp(J))
         if rc:
             raise ValueError("jacobian failed")
         return J
+
+    def rates_cell(self, y, T_iso: float = 300.0, rho: float = 1.0, flux: float = 1.0,
+                   path: float = 0.0):
+        """Every reaction's k and dk/dT for one cell (Arrhenius, tabulated, photo)."""
+        y = np.ascontiguousarray(y, float)
+        k = np.zeros(max(self.nr, 1))
+        dk = np.zeros(max(self.nr, 1))
+        p, keep = self._par(T_iso, 1.0, None, rho, flux, path)
+        rc = lib().ko_rates_cell(self.ptr, _dp(y), ctypes.byref(p), _dp(k), _dp(dk))
+        if rc:
+            raise ValueError("rates failed")
+        return k[:self.nr], dk[:self.nr]
 
     def be_step(self, yn, h, opts: Options, T_iso: float = 300.0, cvtot: float = 1.0):
         yn = np.ascontiguousarray(yn, float)
@@ -182,6 +217,8 @@ class OracleNetwork:
         y = np.ascontiguousarray(cells.y, float)
         T = np.ascontiguousarray(cells.T, float)
         rho = np.ascontiguousarray(cells.rho, float)
+        flux = None if getattr(cells, "flux", None) is None else np.ascontiguousarray(cells.flux, float)
+        path = None if getattr(cells, "path", None) is None else np.ascontiguousarray(cells.path, float)
         yo = np.zeros_like(y)
         To = np.zeros_like(T)
         st = np.zeros(nc, np.int32)
@@ -190,8 +227,10 @@ class OracleNetwork:
         if nthreads is None:
             nthreads = os.cpu_count() or 1
         i32 = ctypes.POINTER(ctypes.c_int32)
-        rc = L.ko_integrate(self.ptr, nc, _dp(y), _dp(T), _dp(rho), float(dt), ctypes.byref(opts),
-                            int(nthreads), _dp(yo), _dp(To), st.ctypes.data_as(i32),
+        opt = lambda a: None if a is None else _dp(a)
+        rc = L.ko_integrate_rad(self.ptr, nc, _dp(y), _dp(T), _dp(rho), opt(flux), opt(path),
+                                float(dt), ctypes.byref(opts),
+                                int(nthreads), _dp(yo), _dp(To), st.ctypes.data_as(i32),
                             nsub.ctypes.data_as(i32), nnew.ctypes.data_as(i32))
         if rc:
             raise ValueError(f"oracle integrate failed: code {rc}")

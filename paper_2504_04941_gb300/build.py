@@ -38,10 +38,21 @@ def _newest_input() -> float:
 
 
 def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
-    """Compile every csrc/*.cu for sm_103a and link lib/libkt.so; returns its path."""
+    """Compile every csrc/*.cu for sm_103a and link lib/libkt.so; returns its path.
+    Concurrent callers (test workers) serialise on a lock file; the later ones find the
+    library up to date."""
+    import fcntl
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
         return LIB
     os.makedirs(os.path.join(LIBDIR, "obj"), exist_ok=True)
+    with open(os.path.join(LIBDIR, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
+            return LIB
+        return _build_locked(verbose, extra_flags)
+
+
+def _build_locked(verbose, extra_flags) -> str:
     cc = nvcc()
 
     def compile_one(src):
@@ -54,7 +65,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             sys.stderr.write(r.stdout + r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, sources()))
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]

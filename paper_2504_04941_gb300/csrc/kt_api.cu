@@ -60,6 +60,15 @@ struct kt_network {
     std::vector<int> nin, nout;                   // [nr]
     std::vector<std::array<int, kt::kMaxSide>> in, out;
     std::vector<double> A, b, th;
+    int cvpoly = 0;                               // heat capacities polynomial in T
+    double t_mid = 0.0;
+    std::vector<double> cvp;                      // [ns*10]: low-range then high-range coefficients
+    std::vector<int> rtype;                       // [nr]: 0 Arrhenius, 1 tabulated, 2 photo
+    std::vector<double> sig_r, sig_s;             // photo cross-sections per reaction / species
+    int ntab = 0, tab_nT = 0, tab_nR = 0;
+    double tab_T0 = 0, tab_T1 = 0, tab_R0 = 0, tab_R1 = 0;
+    std::vector<int> tab_of;                      // [nr]: table row, -1 if none
+    std::vector<double> tab;                      // [ntab][nR][nT] ln k
     std::vector<unsigned char> blob;
     NetView view{};
     const kt_mlp *mlp = nullptr;                  // attached learned-guess MLP (not owned)
@@ -218,7 +227,64 @@ int parse_network(const std::string &text, kt_network *n)
         if (!(t.real(n->A[r]) && t.real(n->b[r]) && t.real(n->th[r]) && t.integer(pair)))
             return fail(KT_EPARSE, "network: reaction %d parameters", r);
     }
-    if (!t.word("end")) return fail(KT_EPARSE, "network: missing 'end'");
+    // optional sections: heat capacities, photo-reactions, rate tables; then "end"
+    n->rtype.assign(n->nr, 0);
+    n->sig_r.assign(n->nr, 0.0);
+    n->sig_s.assign(n->ns, 0.0);
+    n->tab_of.assign(n->nr, -1);
+    for (;;) {
+        if (!t.next(w)) return fail(KT_EPARSE, "network: missing 'end'");
+        if (w == "end") break;
+        if (w == "cv_poly" && !n->cvpoly) {
+            // cv_s(T) = sum_k a_k T^k below t_mid, sum_k b_k T^k from t_mid [J/(mol K)]
+            if (!n->energy) return fail(KT_EPARSE, "network: cv_poly needs the temperature equation");
+            if (!(t.real(n->t_mid) && n->t_mid > 0)) return fail(KT_EPARSE, "network: cv_poly t_mid");
+            n->cvp.resize(static_cast<size_t>(n->ns) * 10);
+            for (int s = 0; s < n->ns; ++s) {
+                int sp = -1;
+                if (!(t.word("cvp") && t.integer(sp) && sp == s)) return fail(KT_EPARSE, "network: cvp line %d", s);
+                for (int k = 0; k < 10; ++k)
+                    if (!t.real(n->cvp[s * 10 + k])) return fail(KT_EPARSE, "network: cvp %d coefficients", s);
+            }
+            n->cvpoly = 1;
+        } else if (w == "photo") {
+            // photo-reactions (Eq. photo-reaction-single): "ph <reaction> <sigma_r>", one reactant
+            int np = -1;
+            if (!(t.integer(np) && np >= 0 && np <= n->nr)) return fail(KT_EPARSE, "network: photo count");
+            for (int i = 0; i < np; ++i) {
+                int r = -1;
+                double sg = -1.0;
+                if (!(t.word("ph") && t.integer(r) && r >= 0 && r < n->nr && t.real(sg) && sg >= 0.0 &&
+                      n->nin[r] == 1 && n->rtype[r] == 0))
+                    return fail(KT_EPARSE, "network: photo-reaction line %d", i);
+                n->rtype[r] = 2;
+                n->sig_r[r] = sg;
+                n->sig_s[n->in[r][0]] += sg;
+            }
+        } else if (w == "rate_table" && n->ntab == 0) {
+            // ln k on log-spaced (T, rho) nodes per tabulated reaction (Sec. 2.2.1 item 3)
+            if (!(t.integer(n->tab_nT) && t.real(n->tab_T0) && t.real(n->tab_T1) && t.integer(n->tab_nR) &&
+                  t.real(n->tab_R0) && t.real(n->tab_R1) && t.integer(n->ntab)) ||
+                n->tab_nT < 2 || n->tab_nT > 64 || n->tab_nR < 1 || n->tab_nR > 64 || n->ntab < 0 ||
+                n->ntab > n->nr || !(n->tab_T0 > 0) || !(n->tab_T1 > n->tab_T0) || !(n->tab_R0 > 0) ||
+                !(n->tab_nR == 1 || n->tab_R1 > n->tab_R0))
+                return fail(KT_EPARSE, "network: rate_table grid");
+            const int m = n->tab_nR * n->tab_nT;
+            n->tab.assign(static_cast<size_t>(n->ntab) * m, 0.0);
+            for (int i = 0; i < n->ntab; ++i) {
+                int r = -1;
+                if (!(t.word("tab") && t.integer(r) && r >= 0 && r < n->nr && n->rtype[r] == 0))
+                    return fail(KT_EPARSE, "network: rate table %d", i);
+                n->rtype[r] = 1;
+                n->tab_of[r] = i;
+                for (int q = 0; q < m; ++q)
+                    if (!t.real(n->tab[static_cast<size_t>(i) * m + q]))
+                        return fail(KT_EPARSE, "network: rate table %d values", i);
+            }
+        } else {
+            return fail(KT_EPARSE, "network: unknown section '%s'", w.c_str());
+        }
+    }
     // element conservation of every reaction (Eq. method-const-elem)
     for (int r = 0; r < n->nr; ++r)
         for (int e = 0; e < n->ne; ++e) {
@@ -270,8 +336,35 @@ void build_blob(kt_network *n)
         if (n->nin[r] != 2 || n->nout[r] != 2) v.shape = 0;
     v.off_rp = o; o = align16(o + 4 * (n->ns + 1));
     v.off_re = o; o = align16(o + 4 * v.nent);
+    v.cvpoly = n->cvpoly;
+    v.t_mid = n->t_mid;
+    v.off_cvp = o;
+    if (n->cvpoly) o = align16(o + 8 * 10 * n->ns);
+    // photo and table descriptors (staged with the rest); the tables themselves follow
+    // the staged part and are read from global memory
+    v.special = 0;
+    v.nphoto = 0;
+    for (int r = 0; r < n->nr; ++r) {
+        if (n->rtype[r] != 0) v.special = 1;
+        if (n->rtype[r] == 2) ++v.nphoto;
+    }
+    v.off_rtype = o; o = align16(o + 4 * n->nr);
+    v.off_sigr = o; o = align16(o + 8 * n->nr);
+    v.off_sigs = o; o = align16(o + 8 * n->ns);
+    v.ntab = n->ntab;
+    v.tab_nT = n->tab_nT;
+    v.tab_nR = n->tab_nR;
+    if (n->ntab) {
+        v.tab_lt0 = std::log(n->tab_T0);
+        v.tab_dlt = (std::log(n->tab_T1) - std::log(n->tab_T0)) / (n->tab_nT - 1);
+        v.tab_lr0 = std::log(n->tab_R0);
+        v.tab_dlr = n->tab_nR > 1 ? std::log(n->tab_R1) - std::log(n->tab_R0) : 1.0;
+    }
     if (o < 16) o = 16;
     v.bytes = o;
+    v.off_tab = o;
+    o = align16(o + 8 * static_cast<int>(n->tab.size()));
+    v.bytes_total = o;
     n->blob.assign(o, 0);
     auto put = [&](int off, int i, double x) { std::memcpy(n->blob.data() + off + 8 * i, &x, 8); };
     for (int r = 0; r < n->nr; ++r) {
@@ -299,6 +392,14 @@ void build_blob(kt_network *n)
     }
     for (int j = 0; j < kt::kExpTable; ++j) put(v.off_exp, j, kt::exp2_table(j));
     std::memcpy(n->blob.data() + v.off_rp, rp.data(), 4 * rp.size());
+    if (n->cvpoly) std::memcpy(n->blob.data() + v.off_cvp, n->cvp.data(), 8 * n->cvp.size());
+    for (int r = 0; r < n->nr; ++r) {
+        const int rt = n->rtype[r] == 1 ? (1 | (n->tab_of[r] << 8)) : n->rtype[r];
+        std::memcpy(n->blob.data() + v.off_rtype + 4 * r, &rt, 4);
+        put(v.off_sigr, r, n->sig_r[r]);
+    }
+    for (int s = 0; s < n->ns; ++s) put(v.off_sigs, s, n->sig_s[s]);
+    if (!n->tab.empty()) std::memcpy(n->blob.data() + v.off_tab, n->tab.data(), 8 * n->tab.size());
     if (!re.empty()) std::memcpy(n->blob.data() + v.off_re, re.data(), 4 * re.size());
     for (int s = 0; s < n->ns; ++s) {
         put(v.off_h, s, n->h[s]);
@@ -316,8 +417,10 @@ int check_opts(const kt_options *o)
         o->max_newton < 1 || (o->form != KT_FORM_FP64 && o->form != KT_FORM_FP32LU) ||
         (o->guess != KT_GUESS_PREV && o->guess != KT_GUESS_MLP && o->guess != KT_GUESS_FULLSTEP) ||
         o->block_warps < 0 ||
-        o->blocks_per_sm < 0)
+        o->blocks_per_sm < 0 || (o->scheme != KT_SCHEME_BE && o->scheme != KT_SCHEME_TRBDF2))
         return fail(KT_EINVAL, "options: a field is out of range");
+    if (o->scheme == KT_SCHEME_TRBDF2 && o->guess == KT_GUESS_MLP)
+        return fail(KT_EINVAL, "options: the learned guess needs scheme KT_SCHEME_BE");
     return KT_OK;
 }
 
@@ -338,6 +441,7 @@ kt::DevOpts dev_opts(const kt_options *o)
     d.retry = o->retry;
     d.atol_mode = o->atol_mode;
     d.guess = o->guess;
+    d.scheme = o->scheme;
     return d;
 }
 
@@ -439,7 +543,8 @@ int state_schedule(kt_state *st, const kt_options *opts, cudaStream_t s, bool la
 int integrate_impl(const kt_network *net, int64_t ncells, const double *y_in, const double *T_in,
                    const double *rho, const double *dt_cell, double dt, const kt_options *opts, double *y_out,
                    double *T_out, int32_t *status, int32_t *n_substeps, int32_t *n_newton, void *scratch,
-                   void *cuda_stream, const kt_mlp *mlp, const int *order = nullptr)
+                   void *cuda_stream, const kt_mlp *mlp, const int *order = nullptr,
+                   const double *flux = nullptr, const double *path = nullptr)
 {
     if (!net) return fail(KT_EINVAL, "kt_integrate: NULL network");
     if (ncells < 0 || !(dt > 0) || !std::isfinite(dt)) return fail(KT_EINVAL, "kt_integrate: bad ncells or dt");
@@ -451,9 +556,11 @@ int integrate_impl(const kt_network *net, int64_t ncells, const double *y_in, co
     if (reinterpret_cast<uintptr_t>(scratch) % 16) return fail(KT_EINVAL, "kt_integrate_ptrs: scratch not 16-B aligned");
     const int N = net->ns + net->energy;
     int cpw = opts->cells_per_warp;
-    if (cpw == 0) cpw = N <= kt::kLaneMaxN ? 32 : 1;
-    if ((cpw != 32 && cpw != 1) || (cpw == 32 && N > kt::kLaneMaxN))
-        return fail(KT_EINVAL, "kt_integrate_ptrs: cells_per_warp %d not available for %d unknowns", cpw, N);
+    // tabulated and photo rates are evaluated by the warp-per-cell kernels
+    if (cpw == 0) cpw = N <= kt::kLaneMaxN && !net->view.special ? 32 : 1;
+    if ((cpw != 32 && cpw != 1) || (cpw == 32 && (N > kt::kLaneMaxN || net->view.special)))
+        return fail(KT_EINVAL, "kt_integrate_ptrs: cells_per_warp %d not available for this network "
+                               "(%d unknowns%s)", cpw, N, net->view.special ? ", tabulated or photo rates" : "");
     if (N > kt::kWarpMaxN)
         return fail(KT_EUNSUPPORTED, "kt_integrate_ptrs: %d unknowns per cell; this build handles up to %d", N,
                     kt::kWarpMaxN);
@@ -471,6 +578,8 @@ int integrate_impl(const kt_network *net, int64_t ncells, const double *y_in, co
     a.dt = dt;
     a.dt_cell = dt_cell;
     a.rho = rho;
+    a.flux = flux;
+    a.path = path;
     a.ncells = ncells;
     if (opts->guess == KT_GUESS_MLP) {
         const kt_mlp *m = mlp ? mlp : net->mlp;
@@ -515,9 +624,9 @@ int kt::prepare_launch(const kt_network *net, int64_t ncells, const double *y_in
     if (ncells > 0 && (!y_in || !T_in || !y_out || !T_out)) return fail(KT_EINVAL, "NULL device buffer");
     const int N = net->ns + net->energy;
     int cpw = opts->cells_per_warp;
-    if (cpw == 0) cpw = N <= kt::kLaneMaxN ? 32 : 1;
-    if ((cpw != 32 && cpw != 1) || (cpw == 32 && N > kt::kLaneMaxN))
-        return fail(KT_EINVAL, "cells_per_warp %d not available for %d unknowns", cpw, N);
+    if (cpw == 0) cpw = N <= kt::kLaneMaxN && !net->view.special ? 32 : 1;
+    if ((cpw != 32 && cpw != 1) || (cpw == 32 && (N > kt::kLaneMaxN || net->view.special)))
+        return fail(KT_EINVAL, "cells_per_warp %d not available for this network (%d unknowns)", cpw, N);
     if (N > kt::kWarpMaxN) return fail(KT_EUNSUPPORTED, "%d unknowns per cell; this build handles up to %d", N, kt::kWarpMaxN);
     *a = kt::LaunchArgs{};
     a->nv = net->view;
@@ -546,6 +655,15 @@ int kt_integrate_ptrs(const kt_network *net, int64_t ncells, const double *y_in,
 {
     return integrate_impl(net, ncells, y_in, T_in, rho, nullptr, dt, opts, y_out, T_out, status, n_substeps,
                           n_newton, scratch, cuda_stream, nullptr);
+}
+
+int kt_integrate_rad(const kt_network *net, int64_t ncells, const double *y_in, const double *T_in,
+                     const double *rho, const double *flux, const double *path, double dt,
+                     const kt_options *opts, double *y_out, double *T_out, int32_t *status,
+                     int32_t *n_substeps, int32_t *n_newton, void *scratch, void *cuda_stream)
+{
+    return integrate_impl(net, ncells, y_in, T_in, rho, nullptr, dt, opts, y_out, T_out, status, n_substeps,
+                          n_newton, scratch, cuda_stream, nullptr, nullptr, flux, path);
 }
 
 int kt_integrate_dt(const kt_network *net, int64_t ncells, const double *y_in, const double *T_in,

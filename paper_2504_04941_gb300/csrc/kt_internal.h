@@ -14,6 +14,15 @@ constexpr int kLaneMaxN = 16;    // unknowns per cell handled by the lane-per-ce
 constexpr int kIdxNone = 255;
 constexpr int kIdxDistinct = 0x80;   // flag in the reactant-count byte: all species differ
 constexpr int kExpTable = 256;       // entries 2^(j/256) of the table-driven exponential
+// The FP32-LU form's simplified Newton converges linearly and stops with an error about
+// as large as its last update, where full Newton (quadratic) stops far below it.  Its
+// absolute Newton tolerance is therefore newton_atol_frac * atol scaled by this factor:
+// trace species below atol then land on full Newton's root to ~1e-9 relative (measured
+// 3e-5 without it on the 32-species network), and the error norm of the step control,
+// weighted by atol, sees a Newton residue below 1e-8 of its weights, so accept/reject
+// decisions agree with full Newton's except within ~1e-8 of the threshold.  The root
+// itself does not change; the cost is ~2 % more iterations on that network.
+constexpr double kF32NewtonAtolScale = 1e-6;
 
 // Byte layout of the device copy of a network ("blob").  Every section starts on a
 // 16-byte boundary so the whole blob can be staged into shared memory by one bulk
@@ -29,15 +38,26 @@ struct NetView {
                                           // nu = net stoichiometric coefficient (nonzero)
     int shape;                            // 22: every reaction has 2 reactants and 2
                                           // products (straight-line rate code); 0: mixed
-    int bytes;                            // total, multiple of 16
-    double t_ref, t_min, t_max;
+    int cvpoly, off_cvp;                  // heat capacities polynomial in T: double[ns*10],
+                                          // cv_s(T) = sum_k c[10s+k] T^k below t_mid,
+                                          // sum_k c[10s+5+k] T^k from t_mid (Sec. 4.2)
+    int special, nphoto;                  // any tabulated or photo rates; photo count
+    int off_rtype;                        // int32[nr]: 0 Arrhenius, 2 photo, 1 | (row << 8) table
+    int off_sigr, off_sigs;               // double[nr] photo cross-sections, double[ns] the
+                                          // species' absorption (sum over its photo reactions)
+    int ntab, tab_nT, tab_nR, off_tab;    // tables: double[ntab][nR][nT] ln k after the staged
+                                          // part (global memory)
+    int bytes;                            // staged part (shared memory), multiple of 16
+    int bytes_total;                      // the whole blob, tables included
+    double t_ref, t_min, t_max, t_mid;
+    double tab_lt0, tab_dlt, tab_lr0, tab_dlr;   // ln T0, ln-T node spacing, ln rho0, ln(rho1/rho0)
 };
 
 // Device copy of the integration options (POD kernel parameter).
 struct DevOpts {
     double rtol, atol, h_init, h_min, newton_rtol, newton_atol_frac;
     double facmax, retry_h_factor, retry_facmax;
-    int max_substeps, max_newton, retry, atol_mode, guess;
+    int max_substeps, max_newton, retry, atol_mode, guess, scheme;
 };
 
 // Scratch words of one integrate call (device memory, 16 B).
@@ -57,6 +77,8 @@ struct LaunchArgs {
     const double *dt_cell;       // per-cell dt (device, may be null: dt for every cell)
     const double *rho;           // per-cell density (device, may be null: 1)
     const unsigned char *mlp;    // packed MLP block for the learned guess (may be null)
+    const double *flux, *path;   // per-cell photo flux factor and path length (may be null:
+                                 // F = 1, dl = 0)
     int mlp_nin, mlp_nout;
     long long ncells;
     const double *y_in, *T_in;
@@ -82,13 +104,16 @@ struct LaneLayout {
     int off_M, off_J, off_V, off_P, off_X;         // matrix / factor / scale / perm / fp32 rhs
     int off_Y, off_YF, off_YH, off_Y2, off_W;      // fp64 vectors
     int off_K;                                     // per-cell rate coefficients (isothermal)
-    int off_FY;                                    // fp32 form: f at the attempt's start state
+    int off_FY;                                    // f at the attempt's start state
+    int off_CV;                                    // C_V(T) of polynomial networks: the cell's
+                                                   // 10 aggregated coefficients (-1: none)
     int warp_bytes;                                // bytes per warp
     int mlp_off;                                   // byte offset of the staged MLP block
     int base;                                      // byte offset of warp 0 (after blob, barriers, MLP)
 };
 
-inline LaneLayout lane_layout(int N, int nr, int energy, int fp32, int blob_bytes, int mlp_bytes = 0)
+inline LaneLayout lane_layout(int N, int nr, int energy, int fp32, int blob_bytes, int mlp_bytes = 0,
+                              int cvpoly = 0)
 {
     LaneLayout L{};
     const int d = 32 * 8, f = 32 * 4;   // bytes per element of a double / 4-byte array
@@ -116,8 +141,9 @@ inline LaneLayout lane_layout(int N, int nr, int energy, int fp32, int blob_byte
     L.off_YH = o; o += N * d;
     L.off_Y2 = o; o += N * d;
     L.off_W = o; o += N * d;
-    if (fp32) { L.off_FY = o; o += N * d; } else { L.off_FY = -1; }
+    L.off_FY = o; o += N * d;      // f at the attempt's start state (FP32 form; TR-BDF2)
     if (!energy) { L.off_K = o; o += nr * d; } else { L.off_K = -1; }
+    if (cvpoly) { L.off_CV = o; o += 10 * d; } else { L.off_CV = -1; }
     L.warp_bytes = (o + 255) & ~255;
     L.mlp_off = (blob_bytes + 16 + 255) & ~255;
     L.base = (L.mlp_off + mlp_bytes + 255) & ~255;
@@ -130,6 +156,7 @@ struct WarpLayout {
     int NP;
     int off_M, off_J, off_V, off_P, off_G;   // matrix, fp32 Jacobian, scales, pivots, gather
     int off_Y, off_YF, off_YH, off_Y2, off_W;
+    int off_F0;                              // TR-BDF2: f at the step's start state
     int off_K, off_DK;                       // rate coefficients and dk/dT per reaction
     int warp_bytes, base;
 };
@@ -157,6 +184,7 @@ inline WarpLayout warp_layout(int N, int nr, int energy, int fp32, int blob_byte
     L.off_YH = take(N * 8);
     L.off_Y2 = take(N * 8);
     L.off_W = take(N * 8);
+    L.off_F0 = take(N * 8);
     L.off_K = take(nr * 8);
     L.off_DK = energy ? take(nr * 8) : -1;
     L.warp_bytes = (o + 127) & ~127;

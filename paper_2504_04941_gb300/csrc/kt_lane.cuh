@@ -41,6 +41,7 @@
 #include "kt_internal.h"
 #include "kt_mlp.cuh"
 #include "kt_tma.cuh"
+#include "kt_trbdf2.cuh"
 
 namespace kt {
 namespace {
@@ -408,10 +409,15 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
     double *YH = reinterpret_cast<double *>(wb + L.off_YH) + lane;
     double *Y2 = reinterpret_cast<double *>(wb + L.off_Y2) + lane;
     double *W = reinterpret_cast<double *>(wb + L.off_W) + lane;
-    double *FY = F32 ? reinterpret_cast<double *>(wb + L.off_FY) + lane : nullptr;
+    double *FY = reinterpret_cast<double *>(wb + L.off_FY) + lane;
     const bool s2 = nv.shape == 22;   // every reaction A + B -> C + D
     int *P = reinterpret_cast<int *>(wb + L.off_P) + lane;
     double *K = ENERGY ? nullptr : reinterpret_cast<double *>(wb + L.off_K) + lane;
+    // C_V(T) of polynomial networks (Sec. 4.2): the cell's coefficients sum_s n0_s c_s,k,
+    // five below t_mid then five from t_mid
+    const bool CVP = ENERGY && nv.cvpoly != 0;
+    double *CV = CVP ? reinterpret_cast<double *>(wb + L.off_CV) + lane : nullptr;
+    const double *cvp = reinterpret_cast<const double *>(sm + nv.off_cvp);
     // FP64 matrix and scales; in the FP32 form they overlay the lane's own J32/M32 and
     // V32/X32 slots and serve the FP64 rescue of a failed FP32 solve
     double *M64 = reinterpret_cast<double *>(wb + L.off_M) + lane;
@@ -450,6 +456,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
     double rho_c = 1.0;
 
     auto finish = [&]() { state = PERSIST ? kNeed : kDone; };
+
+    // TR-BDF2 (o.scheme == KT_SCHEME_TRBDF2, uniform over the launch): phase 0 is the
+    // trapezoidal stage (iterate YF), phase 1 the BDF2 stage (iterate Y2); YH holds the
+    // stage's right-hand side r and FY the rate f(y_n) of the step's start state.
+    const bool TR = o.scheme == KT_SCHEME_TRBDF2;
+    const TrCoef tr = tr_coef();
 
     // Pre-processing (Sec. 2.2.2): floors y >= 0 and T clamped to [t_min, t_max].
     auto load_pre = [&]() {
@@ -607,6 +619,13 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
             b00 += t.cnt[s * ne] * LI(Y, s);
         }
         invCV = ENERGY ? 1.0 / cvt : 0.0;
+        if (CVP) {
+            for (int k = 0; k < 10; ++k) {
+                double c = 0.0;
+                for (int s = 0; s < ns; ++s) c += LI(Y, s) * cvp[s * 10 + k];
+                LI(CV, k) = c;
+            }
+        }
         atol_s = (o.atol_mode == 1 && b00 > 0.0) ? o.atol * b00 : o.atol;
         if (!ENERGY) {
             const double lt = log_t(T_iso, nv.t_ref), invT = 1.0 / T_iso;
@@ -629,6 +648,14 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
 
     // starting point of the current solve (plain predictor / second half from the full step)
     auto restart_solve = [&]() {
+        if (TR) {
+            double *ys = phase == 0 ? YF : Y2;
+            const double *g = phase == 0 ? Y : YF;
+            for (int i = 0; i < N; ++i) LI(ys, i) = LI(g, i);
+            atY = phase == 0;
+            it = 0;
+            return;
+        }
         double *yt = phase == 0 ? YF : (phase == 1 ? YH : Y2);
         const double *g = phase == 2 ? (o.guess != KT_GUESS_PREV ? YF : YH) : Y;
         for (int i = 0; i < N; ++i) LI(yt, i) = LI(g, i);
@@ -697,6 +724,49 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
         }
     };
 
+    // end of a TR-BDF2 step: weighted RMS of the local error estimate, then accept
+    // (growth 0.9 err^(-1/3)) or reject
+    auto step_done_tr = [&]() {
+        const double dh = tr.d * h, inv = 1.0 / dh, ce = 2.0 * tr.C * h;
+        double s2 = 0.0;
+        for (int i = 0; i < N; ++i) {
+            const double yn = LI(Y, i), y1 = LI(Y2, i), f0 = LI(FY, i);
+            const double fg = (LI(YF, i) - yn) * inv - f0;
+            const double f1 = (y1 - LI(YH, i)) * inv;
+            const double est = ce * (tr.a0 * f0 + tr.a1 * fg + tr.a2 * f1);
+            const double sc = (i < ns ? atol_s : 0.0) + o.rtol * fmax(fabs(yn), fabs(y1));
+            const double e = est / sc;
+            s2 += e * e;
+        }
+        const double err = sqrt(s2 / N);
+        if (err <= 1.0) {
+            for (int i = 0; i < N; ++i) LI(Y, i) = LI(Y2, i);
+            fyok = false;
+            jY = false;
+            ++nacc;
+            if (last) {
+                if (post_process()) {
+                    write_out(attempt == 0 ? KT_STATUS_OK : KT_STATUS_RETRIED);
+                    finish();
+                } else {
+                    run_fail();
+                }
+                return;
+            }
+            tt += h;
+            double fac = err > 0.0 ? 0.9 / cbrt(err) : facmax;
+            if (fac > facmax) fac = facmax;
+            if (fac < 0.2) fac = 0.2;
+            h *= fac;
+            if (!begin_attempt()) run_fail();
+        } else {
+            double fac = 0.9 / cbrt(err);
+            if (!(fac >= 0.2)) fac = 0.2;
+            h *= fac;
+            if (h < o.h_min || !begin_attempt()) run_fail();
+        }
+    };
+
     auto phase_done = [&]() {
         usedG = false;
         if (F32 && rescue) {      // the FP64 rescue overwrote the FP32 factors
@@ -704,6 +774,20 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
             needJ = true;
             needF = true;
             refresh = 0;
+        }
+        if (TR) {
+            if (phase == 0) {       // BDF2 stage: r = w1 y_g - w0 y_n, start from y_g
+                phase = 1;
+                it = 0;
+                for (int i = 0; i < N; ++i) {
+                    LI(YH, i) = tr.w1 * LI(YF, i) - tr.w0 * LI(Y, i);
+                    LI(Y2, i) = LI(YF, i);
+                }
+                atY = false;
+            } else {
+                step_done_tr();
+            }
+            return;
         }
         if (phase == 0) {
             phase = 1;
@@ -798,24 +882,44 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
         if (state != kRun) continue;
 
         // ---- one Newton iteration of the current backward-Euler solve
-        const double *yb = phase == 2 ? YH : Y;
-        double *yt = phase == 0 ? YF : (phase == 1 ? YH : Y2);
-        const double hph = phase == 0 ? h : 0.5 * h;
+        const double *yb = TR ? YH : (phase == 2 ? YH : Y);
+        double *yt = TR ? (phase == 0 ? YF : Y2) : (phase == 0 ? YF : (phase == 1 ? YH : Y2));
+        const double hph = TR ? tr.d * h : (phase == 0 ? h : 0.5 * h);
+        // TR-BDF2 stage 1 at its first iterate (y_n itself): f(y_n) -> FY, r1 = y_n + d h f(y_n)
+        const bool trF0 = TR && phase == 0 && atY;
         ++nnew;
         const double T = ENERGY ? LI(yt, ns) : T_iso;
         const bool bad = !(T > 0.0);
-        double lt = 0.0, invT = 0.0;
+        double lt = 0.0, invT = 0.0, invCVi = invCV, dcvr = 0.0;
         if (ENERGY) {
             const double Ts = bad ? 1.0 : T;
             lt = log_t(Ts, nv.t_ref);
             invT = 1.0 / Ts;
+            if (CVP) {
+                // C_V(T) and C_V'(T)/C_V(T) at this iterate (Horner in the range of T)
+                const int o5 = Ts < nv.t_mid ? 5 : 0;
+                const double c0 = LI(CV, 5 - o5), c1 = LI(CV, 6 - o5), c2 = LI(CV, 7 - o5),
+                             c3 = LI(CV, 8 - o5), c4 = LI(CV, 9 - o5);
+                const double cv = (((c4 * Ts + c3) * Ts + c2) * Ts + c1) * Ts + c0;
+                const double dcv = ((4.0 * c4 * Ts + 3.0 * c3) * Ts + 2.0 * c2) * Ts + c1;
+                invCVi = 1.0 / cv;
+                dcvr = dcv * invCVi;
+            }
         }
         if (!F32 || rescue) {
             if (s2)
-                reaction_pass<NT, ENERGY, 1, true>(nv, t, yt, K, lt, invT, invCV, hph, W, M64, nullptr, false);
+                reaction_pass<NT, ENERGY, 1, true>(nv, t, yt, K, lt, invT, invCVi, hph, W, M64, nullptr, false);
             else
-                reaction_pass<NT, ENERGY, 1, false>(nv, t, yt, K, lt, invT, invCV, hph, W, M64, nullptr, false);
+                reaction_pass<NT, ENERGY, 1, false>(nv, t, yt, K, lt, invT, invCVi, hph, W, M64, nullptr, false);
+            // d f_T / d T of C_V(T): -f_T C_V'/C_V, i.e. +h f_T C_V'/C_V in I - h J
+            if (CVP) LI(M64, ns * N + ns) += hph * LI(W, ns) * dcvr;
             if (F32) jY = false;   // the FP64 matrix overlays the FP32 Jacobian
+            if (trF0) {
+                for (int i = 0; i < N; ++i) {
+                    LI(FY, i) = LI(W, i);
+                    LI(YH, i) = LI(Y, i) + hph * LI(W, i);
+                }
+            }
             for (int i = 0; i < N; ++i) LI(W, i) = -(LI(yt, i) - LI(yb, i) - hph * LI(W, i));
             luok = crout_lu<double, 5>(M64, V64, P, N);
             crout_solve<double, 5>(M64, V64, P, W, N);
@@ -825,15 +929,18 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
                 for (int i = 0; i < N; ++i) LI(W, i) = LI(FY, i);
             } else {
                 if (s2)
-                    reaction_pass<NT, ENERGY, 2, true>(nv, t, yt, K, lt, invT, invCV, hph, W, nullptr, J32, doJ);
+                    reaction_pass<NT, ENERGY, 2, true>(nv, t, yt, K, lt, invT, invCVi, hph, W, nullptr, J32, doJ);
                 else
-                    reaction_pass<NT, ENERGY, 2, false>(nv, t, yt, K, lt, invT, invCV, hph, W, nullptr, J32, doJ);
+                    reaction_pass<NT, ENERGY, 2, false>(nv, t, yt, K, lt, invT, invCVi, hph, W, nullptr, J32, doJ);
+                if (CVP && doJ) LIS(J32, ns * N + ns, 6) -= static_cast<float>(LI(W, ns) * dcvr);
                 if (atY) {
                     for (int i = 0; i < N; ++i) LI(FY, i) = LI(W, i);
                     fyok = true;
                 }
                 if (doJ) jY = atY;
             }
+            if (trF0)
+                for (int i = 0; i < N; ++i) LI(YH, i) = LI(Y, i) + hph * LI(FY, i);
             if (needF) {
                 for (int i = 0; i < N; ++i)
                     for (int j = 0; j < N; ++j)
@@ -852,7 +959,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
         // contraction monitors of the FP32 form (FP32 is plenty): dmax = max |delta|/tol,
         // dmaxr = max |delta| / (newton_rtol |y|), the purely relative part
         float dmax = 0.0f, dmaxr = 0.0f;
-        const double natol = natol_frac * atol_s;
+        const double natol = (F32 ? natol_frac * kF32NewtonAtolScale : natol_frac) * atol_s;
         const float natol_f = static_cast<float>(natol);
         for (int i = 0; i < N; ++i) {
             const double d = LI(W, i);
@@ -914,7 +1021,7 @@ template <int NT, bool ENERGY, bool F32, bool PERSIST, bool MLPG>
 int launch_t(const LaunchArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
     const LaneLayout L = lane_layout(a.nv.N, a.nv.nr, a.nv.energy, F32 ? 1 : 0, a.nv.bytes,
-                                     MLPG ? MlpLayout::BYTES : 0);
+                                     MLPG ? MlpLayout::BYTES : 0, a.nv.cvpoly);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -948,32 +1055,30 @@ int launch_t(const LaunchArgs &a, const LaunchCfg &c, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Dispatch over the compile-time options for a fixed (or runtime, NT = 0) size.
-template <int NT>
-int launch_lane_n(const LaunchArgs &a, const LaunchCfg &c, cudaStream_t s)
+// Dispatch over the compile-time options for a fixed (or runtime, NT = 0) size and one
+// form of the iteration matrix.
+template <int NT, bool F32>
+int launch_lane_form(const LaunchArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
-    const bool en = a.nv.energy != 0, f32 = c.form == KT_FORM_FP32LU, per = c.persistent != 0;
+    const bool en = a.nv.energy != 0, per = c.persistent != 0;
     if constexpr (NT == 0 || NT <= kMlpOut) {
-        if (a.mlp) {   // the learned guess runs with the persistent queue only
-            if (en)
-                return f32 ? launch_t<NT, true, true, true, true>(a, c, s) : launch_t<NT, true, false, true, true>(a, c, s);
-            return f32 ? launch_t<NT, false, true, true, true>(a, c, s) : launch_t<NT, false, false, true, true>(a, c, s);
-        }
+        if (a.mlp)   // the learned guess runs with the persistent queue only
+            return en ? launch_t<NT, true, F32, true, true>(a, c, s) : launch_t<NT, false, F32, true, true>(a, c, s);
     } else {
         if (a.mlp) return cudaErrorInvalidValue;
     }
-    if (en) {
-        if (f32) return per ? launch_t<NT, true, true, true, false>(a, c, s) : launch_t<NT, true, true, false, false>(a, c, s);
-        return per ? launch_t<NT, true, false, true, false>(a, c, s) : launch_t<NT, true, false, false, false>(a, c, s);
-    }
-    if (f32) return per ? launch_t<NT, false, true, true, false>(a, c, s) : launch_t<NT, false, true, false, false>(a, c, s);
-    return per ? launch_t<NT, false, false, true, false>(a, c, s) : launch_t<NT, false, false, false, false>(a, c, s);
+    if (en) return per ? launch_t<NT, true, F32, true, false>(a, c, s) : launch_t<NT, true, F32, false, false>(a, c, s);
+    return per ? launch_t<NT, false, F32, true, false>(a, c, s) : launch_t<NT, false, F32, false, false>(a, c, s);
 }
 
 }  // namespace
 
-// Size-specialised launchers (one translation unit each).
+// Launchers of one size (3, 11 or any other N <= 16 as 0) and one form each, every
+// one in its own translation unit (compile time).
 int launch_lane_n3(const LaunchArgs &a, const LaunchCfg &c, void *stream);
-int launch_lane_n11(const LaunchArgs &a, const LaunchCfg &c, void *stream);
+int launch_lane_n11_f64(const LaunchArgs &a, const LaunchCfg &c, void *stream);
+int launch_lane_n11_f32(const LaunchArgs &a, const LaunchCfg &c, void *stream);
+int launch_lane_any_f64(const LaunchArgs &a, const LaunchCfg &c, void *stream);
+int launch_lane_any_f32(const LaunchArgs &a, const LaunchCfg &c, void *stream);
 
 }  // namespace kt

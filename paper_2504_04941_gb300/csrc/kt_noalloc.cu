@@ -69,7 +69,7 @@ extern "C" KT_API int kt_integrate_noalloc(const kt_network *net, int64_t ncells
     int rc = kt::prepare_launch(net, ncells, y_in, T_in, rho, dt, opts, y_out, T_out, status, n_substeps,
                                 n_newton, &a, &c, &host_tables);
     if (rc) return rc;
-    const size_t need = kTablesOffset + static_cast<size_t>(a.nv.bytes);
+    const size_t need = kTablesOffset + static_cast<size_t>(a.nv.bytes_total);
     if (need > kNoAllocBytes) {
         char msg[256];
         std::snprintf(msg, sizeof msg,
@@ -88,7 +88,7 @@ extern "C" KT_API int kt_integrate_noalloc(const kt_network *net, int64_t ncells
     // word, refresh the tables; -1 marks cells a kernel did not reach (a device error)
     cudaError_t e = cudaMemsetAsync(area, 0, sizeof(kt::Scratch), s);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(area + kTablesOffset, host_tables, static_cast<size_t>(a.nv.bytes),
+        e = cudaMemcpyAsync(area + kTablesOffset, host_tables, static_cast<size_t>(a.nv.bytes_total),
                             cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && status) e = cudaMemsetAsync(status, 0xff, static_cast<size_t>(ncells) * sizeof(int32_t), s);
     if (e != cudaSuccess) {

@@ -65,6 +65,16 @@ class Network:
     b: np.ndarray             # [nr]
     theta: np.ndarray         # [nr] K
     pair: np.ndarray          # [nr] index of the reverse entry, -1 if none
+    # temperature-dependent heat capacities (optional): cv_s(T) [J/(mol K)] =
+    # sum_k cv_poly[s, 0, k] T^k below t_mid and sum_k cv_poly[s, 1, k] T^k from t_mid
+    cv_poly: Optional[np.ndarray] = None     # [ns, 2, 5]
+    t_mid: float = 1000.0
+    # photo-reactions (Eq. photo-reaction-single): reaction -> cross-section sigma_r [cm^2]
+    photo: Optional[Dict[int, float]] = None
+    # tabulated rates (Sec. 2.2.1 item 3): grid (nT, T0, T1, nR, rho0, rho1), log-spaced,
+    # and reaction -> ln k on it, shape [nR, nT]
+    table_grid: Optional[Tuple[int, float, float, int, float, float]] = None
+    tables: Optional[Dict[int, np.ndarray]] = None
 
     @property
     def ns(self) -> int:
@@ -104,6 +114,22 @@ class Network:
             out.append(f"reaction {len(self.reac_in[r])} {ins} {len(self.reac_out[r])} {outs} "
                        f"{float(self.A[r])!r} {float(self.b[r])!r} {float(self.theta[r])!r} "
                        f"{int(self.pair[r])}")
+        if self.photo:
+            out.append(f"photo {len(self.photo)}")
+            for r, sg in sorted(self.photo.items()):
+                out.append(f"ph {int(r)} {float(sg)!r}")
+        if self.tables:
+            nT, T0, T1, nR, R0, R1 = self.table_grid
+            out.append(f"rate_table {int(nT)} {float(T0)!r} {float(T1)!r} {int(nR)} {float(R0)!r} "
+                       f"{float(R1)!r} {len(self.tables)}")
+            for r, tab in sorted(self.tables.items()):
+                vals = " ".join(repr(float(v)) for v in np.asarray(tab, float).ravel())
+                out.append(f"tab {int(r)} {vals}")
+        if self.cv_poly is not None:
+            out.append(f"cv_poly {float(self.t_mid)!r}")
+            for sp in range(self.ns):
+                co = " ".join(repr(float(c)) for c in np.asarray(self.cv_poly[sp]).ravel())
+                out.append(f"cvp {sp} {co}")
         out.append("end")
         return "\n".join(out) + "\n"
 
@@ -126,6 +152,68 @@ def _irreversible(name, species, elements, mass, h, cv, counts, energy, t_ref,
         A=np.array([r[2] for r in reactions], float), b=np.array([r[3] for r in reactions], float),
         theta=np.array([r[4] for r in reactions], float),
         pair=np.array([r[5] for r in reactions], np.int64))
+
+
+def with_nasa_heat_capacity(net: Network, seed: int = SEED_BASE + 6, t_mid: float = 1000.0) -> Network:
+    """The network with temperature-dependent heat capacities in the two-range
+    polynomial form of NASA-7 fits (Sec. 4.2: c_V rises above ~10^3 K as vibrational
+    modes activate).  Synthetic coefficients: with u = (T - 300)/700,
+        cv_s(T) = cv_s (1 + e_s (0.3 u^2 + 0.05 u^3 (1 - u)))   below t_mid = 1000 K,
+        cv_s(T) = cv_s (1 + e_s (0.3 + 0.06 (T - 1000)/1000))   from t_mid,
+    e_s ~ U(0.2, 1) (a 20-100 % rise by ~10^4 K; continuous at t_mid, positive for all
+    T > 0), written out as monomial coefficients of T."""
+    rng = np.random.default_rng(seed)
+    e = rng.uniform(0.2, 1.0, net.ns)
+    P = np.polynomial.polynomial
+    u = np.array([-300.0 / 700.0, 1.0 / 700.0])             # u(T) as a polynomial in T
+    low_shape = P.polyadd(0.3 * P.polypow(u, 2), 0.05 * P.polymul(P.polypow(u, 3), P.polysub([1.0], u)))
+    high_shape = np.array([0.3 - 0.06, 0.06 / 1000.0])      # 0.3 + 0.06 (T - 1000)/1000
+    poly = np.zeros((net.ns, 2, 5))
+    for sp in range(net.ns):
+        lo = P.polyadd([1.0], e[sp] * low_shape) * net.cv[sp]
+        hi = P.polyadd([1.0], e[sp] * high_shape) * net.cv[sp]
+        poly[sp, 0, :len(lo)] = lo
+        poly[sp, 1, :len(hi)] = hi
+    return dataclasses.replace(net, name=net.name + "_nasa", cv_poly=poly, t_mid=float(t_mid))
+
+
+def with_tabulated_rates(net: Network, frac: float, seed: int, nT: int = 33, nR: int = 9,
+                         T_range=(5.0, 2.0e5), rho_range=(1e-5, 1e9)) -> Network:
+    """A fraction of the two-body reactions switched to tabulated rates: ln k on a
+    log-spaced (T, rho) grid, sampled from the reaction's own modified-Arrhenius law
+    times a density factor rho^c_r, c_r ~ U(-0.3, 0.3) (a stand-in for the
+    density-dependent rates the paper tabulates, e.g. falloff or escape probabilities;
+    Sec. 2.2.1 item 3).  The Arrhenius parameters stay in the file but are not used."""
+    rng = np.random.default_rng(seed)
+    two = [r for r in range(net.nr) if len(net.reac_in[r]) == 2 and (not net.photo or r not in net.photo)]
+    pick = sorted(rng.choice(two, max(1, int(round(frac * len(two)))), replace=False).tolist())
+    Tn = np.geomspace(T_range[0], T_range[1], nT)
+    Rn = np.geomspace(rho_range[0], rho_range[1], nR)
+    tables = {}
+    for r in pick:
+        c = rng.uniform(-0.3, 0.3)
+        lnk = (math.log(net.A[r]) + net.b[r] * np.log(Tn / net.t_ref) - net.theta[r] / Tn)
+        tables[int(r)] = lnk[None, :] + c * np.log(Rn)[:, None]
+    return dataclasses.replace(net, name=net.name + "_tab", tables=tables,
+                               table_grid=(nT, T_range[0], T_range[1], nR, rho_range[0], rho_range[1]))
+
+
+def with_photo_reactions(net: Network, seed: int) -> Network:
+    """Every one-body reaction becomes a photo-reaction with cross-section
+    sigma_r ~ log-uniform(1e-19, 1e-17) cm^2; its rate is F sigma_r (1 - e^-tau)/tau
+    with the cell's flux factor F and optical depth tau (Eq. photo-reaction-single)."""
+    rng = np.random.default_rng(seed)
+    one = [r for r in range(net.nr) if len(net.reac_in[r]) == 1]
+    photo = {int(r): float(10.0 ** rng.uniform(-19.0, -17.0)) for r in one}
+    return dataclasses.replace(net, name=net.name + "_rad", photo=photo)
+
+
+def radiation_fields(ncells: int, seed: int, flux_range=(1e6, 1e10), path_range=(1e13, 1e17)):
+    """Per-cell photo flux factor F [cm^-2 s^-1] and path length dl [cm], log-uniform."""
+    rng = np.random.default_rng(seed)
+    F = np.exp(rng.uniform(math.log(flux_range[0]), math.log(flux_range[1]), ncells))
+    dl = np.exp(rng.uniform(math.log(path_range[0]), math.log(path_range[1]), ncells))
+    return F, dl
 
 
 def robertson_network() -> Network:
@@ -355,6 +443,10 @@ class Cells:
     y: np.ndarray    # [ns, ncells] SoA, float64
     T: np.ndarray    # [ncells]
     rho: np.ndarray  # [ncells]
+    # photo-reactions (Eq. photo-reaction-single): flux factor F = L dl / dV [cm^-2 s^-1]
+    # and path length dl [cm] per cell; None: F = 1, dl = 0 (optically thin, k = sigma)
+    flux: Optional[np.ndarray] = None
+    path: Optional[np.ndarray] = None
 
     @property
     def ncells(self) -> int:
@@ -362,7 +454,9 @@ class Cells:
 
     def subset(self, idx) -> "Cells":
         idx = np.asarray(idx)
-        return Cells(np.ascontiguousarray(self.y[:, idx]), self.T[idx].copy(), self.rho[idx].copy())
+        pick = lambda a: None if a is None else a[idx].copy()
+        return Cells(np.ascontiguousarray(self.y[:, idx]), self.T[idx].copy(), self.rho[idx].copy(),
+                     pick(self.flux), pick(self.path))
 
 
 def robertson_cells(ncells: int, seed: int = SEED_BASE + 1) -> Cells:
@@ -413,7 +507,7 @@ def gaussian_random_field(n: int, slope: float, seed: int) -> np.ndarray:
     amp = np.zeros_like(kk)
     nz = kk > 0
     amp[nz] = kk[nz] ** (slope / 2.0)
-    g = np.fft.irfftn(fk * amp, s=(n, n, n))
+    g = np.fft.irfftn(fk * amp, s=(n, n, n), axes=(0, 1, 2))
     g = (g - g.mean()) / g.std()
     return g.reshape(-1)
 
@@ -425,11 +519,30 @@ def _normal_cdf(x: np.ndarray) -> np.ndarray:
 
 def combined_cells(net: Network, n_side: int = 160, seed: int = SEED_BASE + 5) -> Cells:
     """GRF T in 50..3000 K (log-uniform marginal) and log10 rho in -4..-1, slope -11/3."""
-    g1 = gaussian_random_field(n_side, -11.0 / 3.0, seed)
-    g2 = gaussian_random_field(n_side, -11.0 / 3.0, seed + 1000)
-    T = 50.0 * 60.0 ** _normal_cdf(g1)
-    log_rho = -4.0 + 3.0 * _normal_cdf(g2)
-    return combustion_cells(net, n_side ** 3, seed=seed + 2000, T=T, log_rho=log_rho)
+    T, log_rho = combined_fields(n_side, seed)
+    return combustion_cells(net, n_side ** 3, seed=seed + 2000, T=T.ravel(), log_rho=log_rho.ravel())
+
+
+def combined_fields(n_side: int = 160, seed: int = SEED_BASE + 5):
+    """(T, log10 rho) of every cell of the n_side^3 Gaussian-random-field grid."""
+    key = (n_side, seed)
+    if key not in _FIELDS:
+        g1 = gaussian_random_field(n_side, -11.0 / 3.0, seed)
+        g2 = gaussian_random_field(n_side, -11.0 / 3.0, seed + 1000)
+        _FIELDS.clear()
+        _FIELDS[key] = (50.0 * 60.0 ** _normal_cdf(g1), -4.0 + 3.0 * _normal_cdf(g2))
+    return _FIELDS[key]
+
+
+_FIELDS: Dict[tuple, tuple] = {}
+
+
+def combined_cells_sample(net: Network, n: int, seed: int = SEED_BASE + 5, n_side: int = 160) -> Cells:
+    """n cells drawn without replacement (seeded) from the n_side^3 random-field grid of
+    combined_cells: the same T and rho fields, compositions drawn as for the grid."""
+    T, log_rho = combined_fields(n_side, seed)
+    idx = np.sort(np.random.default_rng(seed + 3000).choice(n_side ** 3, n, replace=False))
+    return combustion_cells(net, n, seed=seed + 2000, T=T.ravel()[idx], log_rho=log_rho.ravel()[idx])
 
 
 # --------------------------------------------------------------------------- workloads
@@ -456,22 +569,22 @@ class Workload:
     tol: Tolerances
 
 
-FULL_CELLS = {1: 1024, 2: 65536, 3: 1048576, 4: 262144, 5: 160 ** 3}
+FULL_CELLS = {1: 1024, 2: 65536, 3: 1048576, 4: 262144, 5: 160 ** 3, 6: 65536, 7: 65536, 8: 65536}
 
 
 def tolerances(wid: int) -> Tolerances:
     if wid in (1, 4):
         return Tolerances(dt=1.0e4, rtol=1e-6, atol=1e-10, h_init=1e-6, h_min=1e-24)
-    if wid == 2:
+    if wid in (2, 6, 8):
         return Tolerances(dt=1.0e-6, rtol=1e-6, atol=1e-20, h_init=1e-12, h_min=1e-30)
+    if wid == 7:
+        return Tolerances(dt=1.0e10, rtol=1e-6, atol=1e-10, h_init=1e-2, h_min=1e-20,
+                          atol_mode=1)
     if wid == 5:
-        # dt at the scale of a hydrodynamic step; the 64-species cells still take
-        # ~10^3 sub-steps each from their random initial compositions
-        return Tolerances(dt=1.0e-9, rtol=1e-6, atol=1e-20, h_init=1e-13, h_min=1e-30)
+        # dt = 1e-6 s as for the 10-species network (the workload gives none)
+        return Tolerances(dt=1.0e-6, rtol=1e-6, atol=1e-20, h_init=1e-13, h_min=1e-30)
     if wid == 3:
-        # rtol 1e-4: the first-order scheme needs ~1600 sub-steps per active decade at
-        # 1e-6; at 1e-4 the per-cell counts spread ~150..4000 (strong load imbalance)
-        return Tolerances(dt=1.0e10, rtol=1e-4, atol=1e-10, h_init=1e-2, h_min=1e-20,
+        return Tolerances(dt=1.0e10, rtol=1e-6, atol=1e-10, h_init=1e-2, h_min=1e-20,
                           atol_mode=1)
     raise ValueError(wid)
 
@@ -486,6 +599,12 @@ def network(wid: int) -> Network:
     if wid == 5:
         return combustion_network(seed=SEED_BASE + 5, n_species=64, n_elements=4,
                                   n_reversible=500, name="combined64")
+    if wid == 6:
+        return with_nasa_heat_capacity(combustion_network())
+    if wid == 7:
+        return with_tabulated_rates(with_photo_reactions(ism_network(), SEED_BASE + 70), 0.3, SEED_BASE + 71)
+    if wid == 8:
+        return with_tabulated_rates(combustion_network(), 0.2, SEED_BASE + 80)
     raise ValueError(wid)
 
 
@@ -499,14 +618,18 @@ def workload(wid: int, ncells: Optional[int] = None, seed: Optional[int] = None)
     n = FULL_CELLS[wid] if ncells is None else int(ncells)
     if wid in (1, 4):
         cells = robertson_cells(n, s)
-    elif wid == 2:
-        cells = combustion_cells(net, n, s)
+    elif wid in (2, 6, 8):
+        cells = combustion_cells(net, n, SEED_BASE + 2 if seed is None else seed)
+    elif wid == 7:
+        cells = ism_cells(net, n, SEED_BASE + 3 if seed is None else seed)
+        cells.flux, cells.path = radiation_fields(n, s + 1)
     elif wid == 3:
         cells = ism_cells(net, n, s)
     elif wid == 5:
-        if ncells is None:
+        if n >= 160 ** 3:
             cells = combined_cells(net, 160, s)
         else:
-            cells = combustion_cells(net, n, s, t_range=(50.0, 3000.0))
-    names = {1: "robertson", 2: "combustion10", 3: "ism32", 4: "robertson_mlp", 5: "combined64"}
+            cells = combined_cells_sample(net, n, s)
+    names = {1: "robertson", 2: "combustion10", 3: "ism32", 4: "robertson_mlp", 5: "combined64",
+             6: "combustion10_nasa", 7: "ism32_rad", 8: "combustion10_tab"}
     return Workload(wid, names[wid], net, cells, tolerances(wid))

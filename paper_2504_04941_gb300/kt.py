@@ -21,6 +21,8 @@ KT_FORM_FP32LU = 1
 KT_GUESS_PREV = 0
 KT_GUESS_MLP = 1
 KT_GUESS_FULLSTEP = 2
+KT_SCHEME_BE = 0
+KT_SCHEME_TRBDF2 = 1
 STATUS_OK, STATUS_RETRIED, STATUS_REVERTED, STATUS_NONFINITE = 0, 1, 2, 3
 
 _lib = None
@@ -44,7 +46,8 @@ class Options(ctypes.Structure):
                 ("retry", ctypes.c_int), ("atol_mode", ctypes.c_int),
                 ("block_warps", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("cells_per_warp", ctypes.c_int),
-                ("schedule", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("schedule", ctypes.c_int), ("scheme", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 def lib():
@@ -76,6 +79,8 @@ def lib():
                                         ctypes.POINTER(Options), dptr, dptr, dptr, dptr, dptr,
                                         dptr, vp]
         L.kt_scratch_check.argtypes = [vp, vp]
+        L.kt_integrate_rad.argtypes = [vp, c_i64, dptr, dptr, dptr, dptr, dptr, ctypes.c_double,
+                                       ctypes.POINTER(Options), dptr, dptr, dptr, dptr, dptr, vp, vp]
         L.kt_integrate_dt.argtypes = [vp, c_i64, dptr, dptr, dptr, dptr, ctypes.POINTER(Options),
                                       dptr, dptr, dptr, dptr, dptr, dptr, vp]
         L.kt_autotune.argtypes = [vp, c_i64, dptr, dptr, ctypes.c_double, ctypes.POINTER(Options),
@@ -216,11 +221,13 @@ def _stream_handle(stream) -> Optional[int]:
 
 
 def integrate(net: Network, y, T, dt: float, opts: Options, rho=None, out=None,
-              scratch=None, stream=None):
+              scratch=None, stream=None, flux=None, path=None):
     """Integrate cells held in CUDA tensors (float64, y: [ns, ncells] contiguous).
 
     Returns a dict of device tensors y, T, status, nsub, nnewton (``out`` may supply
-    them; passing y/T themselves integrates in place).  Asynchronous on ``stream``."""
+    them; passing y/T themselves integrates in place).  Asynchronous on ``stream``.
+    ``flux`` and ``path`` (CUDA float64 [ncells]) are the photo flux factor and path
+    length of networks with photo-reactions (kt_integrate_rad)."""
     import torch
     ncells = _require_cells(net, y, T, rho, out, scratch)
     dev = T.device
@@ -244,9 +251,16 @@ def integrate(net: Network, y, T, dt: float, opts: Options, rho=None, out=None,
     if scratch is None:
         scratch = torch.empty(scratch_bytes(), dtype=torch.uint8, device=dev)
     _require_cells(net, y, T, rho, dict(y=yo, T=To, status=st, nsub=nsub, nnewton=nnew), scratch)
-    _check(lib().kt_integrate_ptrs(net.ptr, ncells, _ptr(y), _ptr(T), _ptr(rho), float(dt),
-                                   ctypes.byref(opts), _ptr(yo), _ptr(To), _ptr(st), _ptr(nsub),
-                                   _ptr(nnew), _ptr(scratch), _stream_handle(stream)))
+    if flux is None and path is None:
+        _check(lib().kt_integrate_ptrs(net.ptr, ncells, _ptr(y), _ptr(T), _ptr(rho), float(dt),
+                                       ctypes.byref(opts), _ptr(yo), _ptr(To), _ptr(st), _ptr(nsub),
+                                       _ptr(nnew), _ptr(scratch), _stream_handle(stream)))
+    else:
+        _require(flux, "flux", (ncells,), "float64", optional=True)
+        _require(path, "path", (ncells,), "float64", optional=True)
+        _check(lib().kt_integrate_rad(net.ptr, ncells, _ptr(y), _ptr(T), _ptr(rho), _ptr(flux), _ptr(path),
+                                      float(dt), ctypes.byref(opts), _ptr(yo), _ptr(To), _ptr(st),
+                                      _ptr(nsub), _ptr(nnew), _ptr(scratch), _stream_handle(stream)))
     return dict(y=yo, T=To, status=st, nsub=nsub, nnewton=nnew, scratch=scratch)
 
 

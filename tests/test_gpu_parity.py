@@ -87,19 +87,21 @@ def test_combustion_ragged_parity(kt, oracle_mod, form):
     assert np.all(np.abs(E1 - E0) <= 1e-11 * (cv * wl.cells.T + np.abs(net.h) @ y0))
 
 
-@pytest.mark.parametrize("form", [0, 1], ids=["fp64", "fp32lu"])
-def test_combustion_full_size_sampled(kt, oracle_mod, form):
+@pytest.mark.parametrize("form,scheme", [(0, 0), (1, 0), (1, 1)], ids=["fp64", "fp32lu", "fp32lu-trbdf2"])
+def test_combustion_full_size_sampled(kt, oracle_mod, form, scheme):
     """Full 65,536-cell workload, persistent launch as benchmarked; 48 sampled cells."""
     wl = I.workload(2)
-    g = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, kt.options(wl.tol, form=form, persistent=1))
+    g = gpu_run(kt, wl.network, wl.cells, wl.tol.dt,
+                kt.options(wl.tol, form=form, persistent=1, scheme=scheme))
     assert np.all(g["status"] == 0)
     rng = np.random.default_rng(11)
     idx = np.sort(rng.choice(wl.cells.ncells, 48, replace=False))
     sub = wl.cells.subset(idx)
-    o = ora_run(oracle_mod, wl.network, sub, wl.tol.dt, wl.tol)
+    o = ora_run(oracle_mod, wl.network, sub, wl.tol.dt, wl.tol, scheme=scheme)
     gs = {k: (v[:, idx] if v.ndim == 2 else v[idx]) for k, v in g.items()}
     rep = compare(gs, o, wl.network.energy,
-                  tight=tight_oracle(oracle_mod, wl.network, sub, wl.tol.dt, wl.tol, NTHREADS))
+                  tight=tight_oracle(oracle_mod, wl.network, sub, wl.tol.dt, wl.tol, NTHREADS,
+                                     scheme=scheme))
     print(rep)
     assert rep.ok(), rep
     assert conservation_error(wl.network, wl.cells.y, g["y"]) <= 1e-12
@@ -121,16 +123,54 @@ def test_ism_ragged_parity(kt, oracle_mod, form):
 
 @pytest.mark.parametrize("form", [0, 1], ids=["fp64", "fp32lu"])
 def test_combined64_ragged_parity(kt, oracle_mod, form):
-    """64 species + T (65 unknowns, 1000 directed reactions; warp-per-cell), 37 cells."""
+    """64 species + T (65 unknowns, 1000 directed reactions; warp-per-cell), 37 cells.
+    Backward Euler with step doubling over dt/1000 = 1e-9 s (~10^3 sub-steps per cell;
+    the full 1e-6 s interval is covered with TR-BDF2 in test_trbdf2_parity)."""
     wl = I.workload(5, 37)
-    g = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, kt.options(wl.tol, form=form, persistent=1))
-    o = ora_run(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol)
+    dt = wl.tol.dt * 1e-3
+    g = gpu_run(kt, wl.network, wl.cells, dt, kt.options(wl.tol, form=form, persistent=1))
+    o = ora_run(oracle_mod, wl.network, wl.cells, dt, wl.tol)
     rep = compare(g, o, wl.network.energy, rtol=wl.tol.rtol,
-                  tight=tight_oracle(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol, NTHREADS))
+                  tight=tight_oracle(oracle_mod, wl.network, wl.cells, dt, wl.tol, NTHREADS))
     print(rep)
     assert rep.ok(), rep
     assert conservation_error(wl.network, wl.cells.y, g["y"]) <= 1e-12
     assert np.all(g["y"] >= 0)
+
+
+TR_CASES = [(1, None, dict(form=0, persistent=1)), (1, None, dict(form=1, persistent=1)),
+            (1, None, dict(form=0, persistent=1, cells_per_warp=1)),
+            (2, 250, dict(form=0, persistent=0)), (2, 250, dict(form=1, persistent=1)),
+            (2, 250, dict(form=1, persistent=1, cells_per_warp=1)),
+            (3, 97, dict(form=0, persistent=1)), (3, 97, dict(form=1, persistent=1)),
+            (5, 37, dict(form=0, persistent=1)), (5, 37, dict(form=1, persistent=1))]
+TR_IDS = ["robertson-fp64", "robertson-fp32lu", "robertson-warp-fp64", "combustion-fp64",
+          "combustion-fp32lu", "combustion-warp-fp32lu", "ism-fp64", "ism-fp32lu",
+          "combined64-fp64", "combined64-fp32lu"]
+
+
+@pytest.mark.parametrize("wid,n,form", TR_CASES, ids=TR_IDS)
+def test_trbdf2_parity(kt, oracle_mod, wid, n, form):
+    """TR-BDF2 sub-steps (scheme 1) on every workload network and both kernel families,
+    element by element against the oracle running the same scheme."""
+    wl = I.workload(wid, n) if n else I.workload(wid)
+    g = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, kt.options(wl.tol, scheme=1, **form))
+    o = ora_run(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol, scheme=1)
+    rep = compare(g, o, wl.network.energy, rtol=wl.tol.rtol,
+                  tight=tight_oracle(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol, NTHREADS, scheme=1))
+    print(rep)
+    assert rep.ok(), rep
+    assert conservation_error(wl.network, wl.cells.y, g["y"]) <= 1e-12
+    assert np.all(g["y"] >= 0)
+    if wl.network.energy:
+        net = wl.network
+        y0 = np.maximum(wl.cells.y, 0)
+        cv = net.cv @ y0
+        E0 = cv * wl.cells.T + net.h @ y0
+        E1 = cv * g["T"] + net.h @ g["y"]
+        assert np.all(np.abs(E1 - E0) <= 1e-11 * (cv * wl.cells.T + np.abs(net.h) @ y0))
+    if form["form"] == 0 and wid == 1:
+        assert rep.n_flip == 0
 
 
 def test_edge_cases(kt, oracle_mod):
@@ -166,11 +206,11 @@ def test_edge_cases(kt, oracle_mod):
     assert np.array_equal(g["y"], np.maximum(wl.cells.subset(range(3, 40)).y, 0))
 
 
-@pytest.mark.parametrize("form", [0, 1])
-def test_split_range_bit_identical_and_deterministic(kt, form):
+@pytest.mark.parametrize("form,scheme", [(0, 0), (1, 0), (1, 1)])
+def test_split_range_bit_identical_and_deterministic(kt, form, scheme):
     wl = I.workload(2, 200)
     net = kt.Network(wl.network)
-    opts = kt.options(wl.tol, form=form, persistent=1)
+    opts = kt.options(wl.tol, form=form, persistent=1, scheme=scheme)
     a = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, opts, net)
     b = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, opts, net)
     lo = gpu_run(kt, wl.network, wl.cells.subset(range(0, 77)), wl.tol.dt, opts, net)
@@ -179,7 +219,8 @@ def test_split_range_bit_identical_and_deterministic(kt, form):
         assert np.array_equal(a[k], b[k]), k
         assert np.array_equal(a[k], np.concatenate([lo[k], hi[k]], axis=-1)), k
     # persistent and one-pass launches compute the same cells bit for bit
-    c = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, kt.options(wl.tol, form=form, persistent=0), net)
+    c = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, kt.options(wl.tol, form=form, persistent=0, scheme=scheme),
+                net)
     for k in ("y", "T", "status", "nsub", "nnewton"):
         assert np.array_equal(a[k], c[k]), k
 
@@ -212,3 +253,69 @@ def test_state_upload_without_density(kt):
     d = gpu_run(kt, wl.network, wl.cells, wl.tol.dt * 1e-3, opts, net)
     for k in ("y", "T", "status", "nsub", "nnewton"):
         assert np.array_equal(h[k], d[k]), k
+
+
+NASA_CASES = [dict(form=0, persistent=0, scheme=0), dict(form=1, persistent=1, scheme=0),
+              dict(form=0, persistent=1, scheme=1), dict(form=1, persistent=1, scheme=1),
+              dict(form=1, persistent=1, scheme=1, cells_per_warp=1),
+              dict(form=0, persistent=1, scheme=0, cells_per_warp=1)]
+NASA_IDS = ["fp64-be", "fp32lu-be", "fp64-trbdf2", "fp32lu-trbdf2", "warp-fp32lu-trbdf2", "warp-fp64-be"]
+
+
+@pytest.mark.parametrize("form", NASA_CASES, ids=NASA_IDS)
+def test_nasa_heat_capacity_parity(kt, oracle_mod, form):
+    """Temperature-dependent C_V (two-range polynomials, Sec. 4.2) on the combustion
+    network, 250 ragged cells, against the oracle running the same scheme."""
+    wl = I.workload(6, 250)
+    g = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, kt.options(wl.tol, **form))
+    o = ora_run(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol, scheme=form["scheme"])
+    rep = compare(g, o, wl.network.energy,
+                  tight=tight_oracle(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol, NTHREADS,
+                                     scheme=form["scheme"]))
+    print(rep)
+    assert rep.ok(), rep
+    assert conservation_error(wl.network, wl.cells.y, g["y"]) <= 1e-12
+    assert np.all(g["y"] >= 0)
+
+
+RAD_CASES = [(7, 61, dict(form=0, persistent=1, scheme=1)), (7, 61, dict(form=1, persistent=1, scheme=1)),
+             (7, 29, dict(form=0, persistent=1, scheme=0)),
+             (8, 120, dict(form=0, persistent=1, scheme=1)), (8, 120, dict(form=1, persistent=1, scheme=1)),
+             (8, 120, dict(form=1, persistent=0, scheme=0))]
+RAD_IDS = ["ism-rad-fp64-trbdf2", "ism-rad-fp32lu-trbdf2", "ism-rad-fp64-be", "combustion-tab-fp64-trbdf2",
+           "combustion-tab-fp32lu-trbdf2", "combustion-tab-fp32lu-be"]
+
+
+@pytest.mark.parametrize("wid,n,form", RAD_CASES, ids=RAD_IDS)
+def test_tabulated_and_photo_rates_parity(kt, oracle_mod, wid, n, form):
+    """Tabulated (per-cell density slice, ln k linear in ln T) and self-shielded photo
+    rates (k = F sigma (1 - e^-tau)/tau, exact Jacobian) against the oracle: the ISM
+    network with radiation (warp-per-cell), the combustion network with tables (the
+    warp-per-cell kernels take every network with such rates)."""
+    import torch
+    wl = I.workload(wid, n)
+    net = kt.Network(wl.network)
+    c = wl.cells
+    dev = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    r = kt.integrate(net, dev(c.y), dev(c.T), wl.tol.dt, kt.options(wl.tol, **form), rho=dev(c.rho),
+                     flux=dev(c.flux), path=dev(c.path))
+    kt.check_scratch(r["scratch"])
+    g = {k: r[k].cpu().numpy() for k in ("y", "T", "status", "nsub", "nnewton")}
+    o = ora_run(oracle_mod, wl.network, c, wl.tol.dt, wl.tol, scheme=form["scheme"])
+    rep = compare(g, o, wl.network.energy, rtol=wl.tol.rtol,
+                  tight=tight_oracle(oracle_mod, wl.network, c, wl.tol.dt, wl.tol, NTHREADS, scheme=form["scheme"]))
+    print(rep)
+    assert rep.ok(), rep
+    assert conservation_error(wl.network, c.y, g["y"]) <= 1e-12
+    assert np.all(g["y"] >= 0)
+
+
+def test_special_rates_refuse_the_lane_kernels(kt):
+    import torch
+    wl = I.workload(8, 4)
+    net = kt.Network(wl.network)
+    y = torch.from_numpy(wl.cells.y).cuda()
+    T = torch.from_numpy(wl.cells.T).cuda()
+    with pytest.raises(kt.KtError) as ei:
+        kt.integrate(net, y, T, 1e-9, kt.options(wl.tol, cells_per_warp=32))
+    assert ei.value.code == -1

@@ -139,3 +139,29 @@ def test_longest_first_schedule_changes_no_result(kt, wid, n, dt_scale):
         out = fresh.download()
         for k in ref:
             assert np.array_equal(out[k], ref[k]), (form, "fresh", k)
+
+
+def test_caller_cost_estimate_orders_queue_without_changing_results(kt):
+    """kt_state_set_cost: any caller-given cost estimate (host or device) only reorders
+    the persistent queue; with graph replay and both schemes every output equals the
+    index-order launch bit for bit, and the state's counters then hold the measured
+    Newton counts."""
+    import torch
+    n = 300
+    wl = I.workload(2, n)
+    dt = wl.tol.dt * 1e-2
+    net = kt.Network(wl.network)
+    st = kt.State(net, n)
+    rng = np.random.default_rng(5)
+    for scheme in (0, 1):
+        ref = _direct(kt, net, wl.cells, dt, kt.options(wl.tol, form=1, persistent=1, scheme=scheme))
+        costs = [np.arange(n, dtype=np.int32)[::-1].copy(),
+                 torch.from_numpy(rng.integers(0, 10000, n).astype(np.int32)).cuda()]
+        for cost in costs:
+            opts = kt.options(wl.tol, form=1, persistent=1, use_graph=1, schedule=1, scheme=scheme)
+            st.set_cost(cost)
+            st.upload(wl.cells.y, wl.cells.T, wl.cells.rho)
+            st.integrate(dt, opts)
+            out = st.download()
+            for k in ref:
+                assert np.array_equal(out[k], ref[k]), (scheme, k)

@@ -29,7 +29,13 @@ MUTANTS = [
      "dkdT[r] = k[r] * (n->b[r] - n->theta[r] / T) / T;"),
     ("arrhenius_sign", "double arg = n->b[r] * lt - n->theta[r] / T;",
      "double arg = n->b[r] * lt + n->theta[r] / T;"),
-    ("energy_sign", "f[n->ns] = -q / cvtot;", "f[n->ns] = q / cvtot;"),
+    ("energy_sign", "f[n->ns] = -q / heat_capacity(n, hc, y[n->ns], &dcv);",
+     "f[n->ns] = q / heat_capacity(n, hc, y[n->ns], &dcv);"),
+    ("cv_poly_dT_term_sign", "J[n->ns * N + n->ns] -= f[n->ns] * dcv / cv;",
+     "J[n->ns * N + n->ns] += f[n->ns] * dcv / cv;"),
+    ("cv_poly_range_swapped", "const double *a = n->cvp + s * 10 + (T < n->t_mid ? 0 : 5);",
+     "const double *a = n->cvp + s * 10 + (T < n->t_mid ? 5 : 0);"),
+    ("cv_poly_derivative_index", "if (k < 4) dv += (k + 1) * a[k + 1] * tk;", "if (k < 4) dv += k * a[k + 1] * tk;"),
     ("lu_no_swap", "if (imax != j) {\n            for (k = 0; k < N; k++) {",
      "if (0) {\n            for (k = 0; k < N; k++) {"),
     ("lu_unscaled_pivot", [("double t = fabs(a[i * N + j]) / v[i];", "double t = fabs(a[i * N + j]);"),
@@ -58,6 +64,13 @@ MUTANTS = [
     ("trbdf2_estimate_scale", "const double ce = 2.0 * k.C * h;", "const double ce = k.C * h;"),
     ("trbdf2_estimate_fg_sign", "double fg = (yg[i] - yn[i]) * inv - f0[i];",
      "double fg = (yg[i] - yn[i]) * inv + f0[i];"),
+    ("table_slope_without_T", "*dk = *k * ((L[j + 1] - L[j]) / dl) / T;", "*dk = *k * ((L[j + 1] - L[j]) / dl);"),
+    ("table_rho_weights_swapped", "ltab[t * nT + j] = nR > 1 ? (1.0 - w) * row[j] + w * row[nT + j] : row[j];",
+     "ltab[t * nT + j] = nR > 1 ? w * row[j] + (1.0 - w) * row[nT + j] : row[j];"),
+    ("table_segment_off_by_one", "*k = exp(L[j] + fr * (L[j + 1] - L[j]));", "*k = exp(L[j + 1] + fr * (L[j + 1] - L[j]));"),
+    ("photo_phi_sign", "*phi = (1.0 - e) / tau;", "*phi = (1.0 + e) / tau;"),
+    ("photo_depth_without_path", "return rd->path * s;", "return s;"),
+    ("photo_jacobian_dropped", "J[in[0] * N + m] -= d;", "(void)d;"),
     ("accept_wrong_norm_weight", "double sc = eatol(c, i) + c->o->rtol * fmax(fabs(y[i]), fabs(y2[i]));",
      "double sc = eatol(c, i) + c->o->rtol * fabs(y[i]) * 1e3;"),
 ]
@@ -114,16 +127,19 @@ def _pins(m):
         return rc == 0 and perm[0] == 1
 
     def jac_fd():
-        for wid in (1, 2):
+        for wid in (1, 2, 6):
             netw = I.network(wid)
             net = m.OracleNetwork(netw)
             wl = I.workload(wid, 3)
             y = wl.cells.y[:, 1].copy()
+            n0 = y.copy() if netw.cv_poly is not None else None
             T = float(wl.cells.T[1])
+            if wid == 6:
+                T = 1400.0            # above t_mid: the high-range polynomial
             cv = float(netw.cv @ y) if netw.energy else 1.0
             if netw.energy:
                 y = np.append(y, T)
-            J = net.jacobian(y, T, cv)
+            J = net.jacobian(y, T, cv, n0)
             s = np.maximum(np.abs(y), 1e-6 * np.abs(y).max())
             F = np.zeros_like(J)
             for k in range(len(y)):
@@ -131,7 +147,7 @@ def _pins(m):
                 yp, ym = y.copy(), y.copy()
                 yp[k] += h
                 ym[k] -= h
-                F[:, k] = (net.rhs(yp, T, cv) - net.rhs(ym, T, cv)) / (2 * h)
+                F[:, k] = (net.rhs(yp, T, cv, n0) - net.rhs(ym, T, cv, n0)) / (2 * h)
             Js, Fs = J * s[None, :], F * s[None, :]
             sc = np.maximum(np.abs(Js), np.abs(Fs)).max(axis=1, keepdims=True) + 1e-300
             if np.any(np.abs(Js - Fs) > 1e-6 * sc):
@@ -238,7 +254,72 @@ def _pins(m):
         return (3.7 < errs[0] / errs[1] < 4.3 and rc == 0 and
                 bool(np.all(np.abs(est / true - 1.0) < 0.04)))
 
-    for name, fn in (("lu_exact", lu_exact), ("post_process", post_process), ("trbdf2", trbdf2), ("lu_pivot", lu_pivot), ("jac_fd", jac_fd),
+    def cv_poly_energy():
+        # E(T) + sum h n at the end of a long interval vs the antiderivative of C_V (both
+        # ranges crossed: cells start at 900-2500 K)
+        wl = I.workload(6, 3)
+        netw = wl.network
+        P = np.polynomial.polynomial
+        r = m.OracleNetwork(netw).integrate(wl.cells, wl.tol.dt, m.options(wl.tol, scheme=1), 1)
+        for c in range(3):
+            y0 = np.maximum(wl.cells.y[:, c], 0)
+            lo = P.polyint(np.einsum("s,sk->k", y0, netw.cv_poly[:, 0, :]))
+            hi = P.polyint(np.einsum("s,sk->k", y0, netw.cv_poly[:, 1, :]))
+
+            def E(T):
+                tm = netw.t_mid
+                return P.polyval(min(T, tm), lo) + (P.polyval(T, hi) - P.polyval(tm, hi) if T > tm else 0.0)
+            dE = E(r["T"][c]) - E(wl.cells.T[c]) + netw.h @ (r["y"][:, c] - y0)
+            if not abs(dE) <= 1e-4 * (np.abs(netw.h) @ y0):
+                return False
+        return True
+
+    def tables_photo():
+        import dataclasses
+        # density reduction and the T slope of a tabulated rate
+        base = I.robertson_network()
+        Rn = np.geomspace(1e-2, 1e2, 5)
+        lnk = math.log(2e-3) + 0.37 * np.log(Rn)[:, None] + 0.5 * np.sin(np.arange(7))[None, :]
+        net = m.OracleNetwork(dataclasses.replace(base, tables={0: lnk}, table_grid=(7, 10.0, 1e4, 5, 1e-2, 1e2)))
+        k, _ = net.rates_cell(np.ones(3), T_iso=np.geomspace(10.0, 1e4, 7)[3], rho=0.013)
+        ok = abs(k[0] / (math.exp(math.log(2e-3) + 0.5 * math.sin(3)) * 0.013 ** 0.37) - 1) < 1e-12
+        k, dk = net.rates_cell(np.ones(3), T_iso=123.0, rho=2.0)
+        kp, _ = net.rates_cell(np.ones(3), T_iso=123.0001, rho=2.0)
+        km, _ = net.rates_cell(np.ones(3), T_iso=122.9999, rho=2.0)
+        ok = ok and abs(dk[0] / ((kp[0] - km[0]) / 2e-4) - 1) < 1e-6
+        # photolysis closed form
+        sig, F, dl = 1e-18, 1e8, 1e17
+        ph = I._irreversible("photolysis", ["X", "Y"], ["E"], [1.0, 1.0], [0.0, 0.0], [1.0, 1.0],
+                             [[1], [1]], 0, 300.0, 10.0, 1e5, [((0,), (1,), 1.0, 0.0, 0.0, -1)])
+        pn = m.OracleNetwork(dataclasses.replace(ph, photo={0: sig}))
+        a, n0, t = dl * sig, 1.0 / (dl * sig), 2.0 / (sig * F)
+        cells = I.Cells(np.array([[n0], [0.0]]), np.array([300.0]), np.array([1.0]), np.array([F]), np.array([dl]))
+        r = pn.integrate(cells, t, m.options(rtol=1e-9, atol=1e-12 * n0, h_init=1e-6 * t, scheme=1), 1)
+        exact = math.log1p(math.expm1(a * n0) * math.exp(-sig * F * t)) / a
+        ok = ok and abs(r["y"][0, 0] / exact - 1) < 1e-5
+        # Jacobian of the radiation workload network by central differences
+        netw = I.network(7)
+        wn = m.OracleNetwork(netw)
+        wl = I.workload(7, 2)
+        y = wl.cells.y[:, 0].copy()
+        kw = dict(rho=float(wl.cells.rho[0]), flux=float(wl.cells.flux[0]), path=float(wl.cells.path[0]))
+        J = wn.jacobian(y, float(wl.cells.T[0]), 1.0, None, **kw)
+        Jfd = np.zeros_like(J)
+        for mm in range(len(y)):
+            h = 1e-6 * max(abs(y[mm]), 1e-6 * np.abs(y).max())
+            yp, ym = y.copy(), y.copy()
+            yp[mm] += h
+            ym[mm] -= h
+            Jfd[:, mm] = (wn.rhs(yp, float(wl.cells.T[0]), 1.0, None, **kw) -
+                          wn.rhs(ym, float(wl.cells.T[0]), 1.0, None, **kw)) / (2 * h)
+        s_ = np.maximum(np.abs(y), 1e-6 * np.abs(y).max())
+        Js, Fs = J * s_[None, :], Jfd * s_[None, :]
+        sc = np.maximum(np.abs(Js), np.abs(Fs)).max(axis=1, keepdims=True) + 1e-300
+        return bool(ok and np.all(np.abs(Js - Fs) <= 1e-6 * sc))
+
+    for name, fn in (("lu_exact", lu_exact), ("post_process", post_process), ("trbdf2", trbdf2),
+                     ("tables_photo", tables_photo),
+                     ("cv_poly_energy", cv_poly_energy), ("lu_pivot", lu_pivot), ("jac_fd", jac_fd),
                      ("rhs_robertson", rhs_robertson), ("rates_printed", rates_printed),
                      ("fixed_step_chain", fixed_step_chain), ("bateman", bateman),
                      ("single_step_two_halves", single_step_two_halves),

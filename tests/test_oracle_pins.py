@@ -155,7 +155,7 @@ def test_rhs_robertson_textbook(oracle_mod):
         assert np.allclose(f, ref, rtol=1e-14, atol=1e-17)
 
 
-def _fd_jacobian(net, y, T_iso, cvtot):
+def _fd_jacobian(net, y, T_iso, cvtot, n0=None):
     n = len(y)
     J = np.zeros((n, n))
     floor = 1e-6 * np.abs(y).max()
@@ -164,23 +164,25 @@ def _fd_jacobian(net, y, T_iso, cvtot):
         yp, ym = y.copy(), y.copy()
         yp[m] += h
         ym[m] -= h
-        J[:, m] = (net.rhs(yp, T_iso, cvtot) - net.rhs(ym, T_iso, cvtot)) / (2 * h)
+        J[:, m] = (net.rhs(yp, T_iso, cvtot, n0) - net.rhs(ym, T_iso, cvtot, n0)) / (2 * h)
     return J
 
 
-@pytest.mark.parametrize("wid", [1, 2, 3, 5])
+@pytest.mark.parametrize("wid", [1, 2, 3, 5, 6])
 def test_jacobian_vs_central_differences(oracle_mod, wid):
+    """Workload 6 has C_V(T): its temperature row carries the dC_V/dT term."""
     netw = I.network(wid)
     net = oracle_mod.OracleNetwork(netw)
-    wl = I.workload(wid, 6) if wid != 5 else I.workload(5, 6)
+    wl = I.workload(wid, 6)
     for c in range(3):
         y = wl.cells.y[:, c].copy()
+        n0 = y.copy() if netw.cv_poly is not None else None
         T = float(wl.cells.T[c])
         cvtot = float(np.dot(netw.cv, y)) if netw.energy else 1.0
         if netw.energy:
             y = np.append(y, T)
-        J = net.jacobian(y, T, cvtot)
-        Jfd = _fd_jacobian(net, y, T, cvtot)
+        J = net.jacobian(y, T, cvtot, n0)
+        Jfd = _fd_jacobian(net, y, T, cvtot, n0)
         # columns times their variable's scale: every entry of a row is then the response
         # of f_i to a relative change of one unknown (same units along the row), so a
         # thermal-coupling term cannot hide behind the row's species entries
@@ -629,3 +631,216 @@ def test_trbdf2_conservation(oracle_mod, wid):
         E0 = cv * wl.cells.T + netw.h @ y0
         E1 = cv * r["T"] + netw.h @ r["y"]
         assert np.all(np.abs(E1 - E0) <= 1e-12 * (cv * wl.cells.T + np.abs(netw.h) @ y0))
+
+
+
+# ------------------------------------------------------------------ C_V(T) (Sec. 4.2)
+
+
+def _cv_antiderivative(netw, n0, T):
+    """E(T) = integral_0^T C_V(T') dT' for C_V(T) = sum_s n0_s cv_s(T), piecewise, by
+    numpy's exact polynomial integration (independent of the oracle's evaluation)."""
+    P = np.polynomial.polynomial
+    lo = np.einsum("s,sk->k", n0, netw.cv_poly[:, 0, :])
+    hi = np.einsum("s,sk->k", n0, netw.cv_poly[:, 1, :])
+    Ilo, Ihi = P.polyint(lo), P.polyint(hi)
+    tm = netw.t_mid
+    T = np.asarray(T, float)
+    below = P.polyval(np.minimum(T, tm), Ilo)
+    above = np.where(T > tm, P.polyval(np.maximum(T, tm), Ihi) - P.polyval(tm, Ihi), 0.0)
+    return below + above
+
+
+def test_cv_poly_constant_reproduces_constant_network(oracle_mod):
+    """Polynomials that are constants (a0 = cv_s) give bit for bit the constant-C_V run."""
+    import dataclasses
+    base = I.network(2)
+    poly = np.zeros((base.ns, 2, 5))
+    poly[:, 0, 0] = poly[:, 1, 0] = base.cv
+    flat = dataclasses.replace(base, cv_poly=poly)
+    wl = I.workload(2, 4)
+    for scheme in (0, 1):
+        opts = oracle_mod.options(wl.tol, scheme=scheme)
+        a = oracle_mod.OracleNetwork(base).integrate(wl.cells, wl.tol.dt * 1e-2, opts, 2)
+        b = oracle_mod.OracleNetwork(flat).integrate(wl.cells, wl.tol.dt * 1e-2, opts, 2)
+        for k in ("y", "T", "nsub", "nnewton", "status"):
+            assert np.array_equal(a[k], b[k]), (scheme, k)
+
+
+def test_cv_poly_energy_balance(oracle_mod):
+    """With C_V(T) the energy E(T) + sum_s h_s n_s, E the antiderivative of C_V, is
+    conserved by the ODE; it is nonlinear in T, so the scheme keeps it to its
+    discretisation error, which shrinks with rtol (TR-BDF2: ~rtol^(2/3))."""
+    wl = I.workload(6, 6)
+    netw = wl.network
+    net = oracle_mod.OracleNetwork(netw)
+    y0 = np.maximum(wl.cells.y, 0.0)
+    res = []
+    for rtol in (1e-6, 1e-9):
+        r = net.integrate(wl.cells, wl.tol.dt, oracle_mod.options(wl.tol, scheme=1, rtol=rtol,
+                                                                  max_substeps=2000000), 2)
+        assert np.all(r["status"] == 0)
+        worst = 0.0
+        for c in range(wl.cells.ncells):
+            dE = (_cv_antiderivative(netw, y0[:, c], r["T"][c]) - _cv_antiderivative(netw, y0[:, c], wl.cells.T[c])
+                  + netw.h @ (r["y"][:, c] - y0[:, c]))
+            scale = np.abs(netw.h) @ y0[:, c]
+            worst = max(worst, abs(dE) / scale)
+        res.append(worst)
+    assert res[0] <= 1e-6 and res[1] <= 1e-8 and res[1] < res[0] / 30, res
+
+
+def test_cv_poly_lowers_the_temperature_rise(oracle_mod):
+    """The synthetic C_V(T) is above the constant C_V at every T, so the same heat
+    release raises T less (the paper's frozen-C_V control overpredicts T by ~15 %)."""
+    wl = I.workload(6, 6)
+    const = I.workload(2, 6)
+    a = oracle_mod.OracleNetwork(wl.network).integrate(wl.cells, wl.tol.dt, oracle_mod.options(wl.tol, scheme=1), 2)
+    b = oracle_mod.OracleNetwork(const.network).integrate(const.cells, wl.tol.dt, oracle_mod.options(wl.tol, scheme=1), 2)
+    assert np.array_equal(wl.cells.y, const.cells.y) and np.array_equal(wl.cells.T, const.cells.T)
+    rise_poly, rise_const = a["T"] - wl.cells.T, b["T"] - wl.cells.T
+    hot = rise_const > 100.0
+    assert hot.any()
+    assert np.all(rise_poly[hot] < rise_const[hot])
+
+
+# ------------------------------------------------------------------ tabulated and photo rates
+
+
+def test_table_linear_in_log_T_reproduces_arrhenius(oracle_mod):
+    """ln k linear in ln T (theta = 0) is interpolated exactly, so a tabulated copy of
+    such reactions integrates like the Arrhenius network (rounding only), rates, dk/dT
+    and the energy equation included."""
+    import dataclasses
+    base = I.network(2)
+    theta = base.theta.copy()
+    pick = [0, 3, 7, 12, 20]
+    theta[pick] = 0.0
+    arr = dataclasses.replace(base, theta=theta)
+    Tn = np.geomspace(5.0, 2e5, 17)
+    tables = {r: np.tile(math.log(base.A[r]) + base.b[r] * np.log(Tn / base.t_ref), (3, 1)) for r in pick}
+    tab = dataclasses.replace(arr, tables=tables, table_grid=(17, 5.0, 2e5, 3, 1e-6, 1e2))
+    a, b = oracle_mod.OracleNetwork(arr), oracle_mod.OracleNetwork(tab)
+    for T in (37.0, 950.0, 2345.6, 7777.0):
+        y = np.append(np.ones(base.ns), T)           # the energy network reads T from y
+        ka, dka = a.rates_cell(y, rho=0.3)
+        kb, dkb = b.rates_cell(y, rho=0.3)
+        assert np.allclose(kb, ka, rtol=1e-13, atol=0) and np.allclose(dkb, dka, rtol=1e-12, atol=0)
+    wl = I.workload(2, 4)
+    ra = a.integrate(wl.cells, wl.tol.dt, oracle_mod.options(wl.tol, scheme=1), 2)
+    rb = b.integrate(wl.cells, wl.tol.dt, oracle_mod.options(wl.tol, scheme=1), 2)
+    assert np.allclose(rb["y"], ra["y"], rtol=1e-9, atol=1e-30)
+    assert np.allclose(rb["T"], ra["T"], rtol=1e-11)
+
+
+def test_table_density_reduction_and_slope(oracle_mod):
+    """Pre-processing reduces the (T, rho) table at the cell's density: ln k linear in
+    ln rho comes out exactly; inside a T segment dk/dT equals the central difference
+    of k, and beyond the grid k is the end value with dk/dT = 0."""
+    import dataclasses
+    base = I.robertson_network()
+    Tn = np.geomspace(10.0, 1e4, 7)
+    Rn = np.geomspace(1e-2, 1e2, 5)
+    c, a0 = 0.37, math.log(2e-3)
+    lnk = a0 + c * np.log(Rn)[:, None] + 0.5 * np.sin(np.arange(7))[None, :]
+    net = oracle_mod.OracleNetwork(dataclasses.replace(base, tables={0: lnk},
+                                                      table_grid=(7, 10.0, 1e4, 5, 1e-2, 1e2)))
+    y = np.ones(3)
+    for rho in (0.013, 1.0, 47.0):
+        k, _ = net.rates_cell(y, T_iso=Tn[3], rho=rho)
+        assert k[0] == pytest.approx(math.exp(a0 + 0.5 * math.sin(3)) * rho ** c, rel=1e-13)
+    T, h = 123.0, 1e-4
+    k, dk = net.rates_cell(y, T_iso=T, rho=2.0)
+    kp, _ = net.rates_cell(y, T_iso=T + h, rho=2.0)
+    km, _ = net.rates_cell(y, T_iso=T - h, rho=2.0)
+    assert dk[0] == pytest.approx((kp[0] - km[0]) / (2 * h), rel=1e-6)
+    k_lo, dk_lo = net.rates_cell(y, T_iso=3.0, rho=2.0)
+    k_hi, dk_hi = net.rates_cell(y, T_iso=5e4, rho=2.0)
+    k0, _ = net.rates_cell(y, T_iso=10.0, rho=2.0)
+    k6, _ = net.rates_cell(y, T_iso=1e4, rho=2.0)
+    assert k_lo[0] == pytest.approx(k0[0], rel=1e-14) and dk_lo[0] == 0.0
+    assert k_hi[0] == pytest.approx(k6[0], rel=1e-14) and dk_hi[0] == 0.0
+
+
+def _photolysis_network(sigma):
+    """X -> Y by photo-dissociation (cross-section sigma), one element shared."""
+    return I._irreversible("photolysis", ["X", "Y"], ["E"], [1.0, 1.0], [0.0, 0.0], [1.0, 1.0],
+                           [[1], [1]], 0, 300.0, 10.0, 1e5, [((0,), (1,), 1.0, 0.0, 0.0, -1)])
+
+
+def test_photo_rate_thin_limit_and_shielding(oracle_mod):
+    """k = F sigma (1 - e^-tau)/tau with tau = dl sum n sigma: F sigma when dl = 0,
+    F sigma / tau when tau >> 1 (Eq. photo-reaction-single)."""
+    import dataclasses
+    sig, F = 3e-18, 2e9
+    net = oracle_mod.OracleNetwork(dataclasses.replace(_photolysis_network(sig), photo={0: sig}))
+    k, dk = net.rates_cell(np.array([1e4, 0.0]), flux=F, path=0.0)
+    assert k[0] == F * sig and dk[0] == 0.0
+    for n, dl in ((1e4, 1e10), (1e5, 1e16), (1e8, 1e18)):
+        tau = dl * n * sig
+        k, _ = net.rates_cell(np.array([n, 0.0]), flux=F, path=dl)
+        assert k[0] == pytest.approx(F * sig * -math.expm1(-tau) / tau, rel=1e-13)
+
+
+@pytest.mark.parametrize("tau0", [1e-3, 1.0, 30.0])
+def test_photolysis_closed_form(oracle_mod, tau0):
+    """dn/dt = -F sigma phi(a n) n = -(F/dl)(1 - e^{-a n}), a = dl sigma, integrates to
+    n(t) = ln(1 + (e^{a n0} - 1) e^{-sigma F t}) / a.  TR-BDF2 at rtol 1e-9 matches it
+    to its own accuracy; X + Y stays exact."""
+    import dataclasses
+    sig, F, dl = 1e-18, 1e8, 1e17
+    net = oracle_mod.OracleNetwork(dataclasses.replace(_photolysis_network(sig), photo={0: sig}))
+    a = dl * sig
+    n0 = tau0 / a
+    t = 2.0 / (sig * F)
+    cells = I.Cells(np.array([[n0], [0.0]]), np.array([300.0]), np.array([1.0]),
+                    np.array([F]), np.array([dl]))
+    r = net.integrate(cells, t, oracle_mod.options(rtol=1e-9, atol=1e-30 + 1e-12 * n0, h_init=1e-6 * t,
+                                                   scheme=1), 1)
+    assert r["status"][0] == 0
+    exact = math.log1p(math.expm1(a * n0) * math.exp(-sig * F * t)) / a
+    assert r["y"][0, 0] == pytest.approx(exact, rel=1e-5)
+    assert r["y"][:, 0].sum() == pytest.approx(n0, rel=1e-14)
+
+
+@pytest.mark.parametrize("wid", [7, 8])
+def test_jacobian_with_tables_and_photo(oracle_mod, wid):
+    """Central differences of f on the radiation (photo + tabulated) and tabulated
+    workload networks, at each cell's density, flux and path length."""
+    netw = I.network(wid)
+    net = oracle_mod.OracleNetwork(netw)
+    wl = I.workload(wid, 4)
+    for c in range(3):
+        y = wl.cells.y[:, c].copy()
+        T = float(wl.cells.T[c])
+        kw = dict(rho=float(wl.cells.rho[c]))
+        if wl.cells.flux is not None:
+            kw.update(flux=float(wl.cells.flux[c]), path=float(wl.cells.path[c]))
+        cvtot = float(np.dot(netw.cv, y)) if netw.energy else 1.0
+        if netw.energy:
+            y = np.append(y, T)
+        J = net.jacobian(y, T, cvtot, None, **kw)
+        Jfd = np.zeros_like(J)
+        floor = 1e-6 * np.abs(y).max()
+        for m in range(len(y)):
+            h = 1e-6 * max(abs(y[m]), floor)
+            yp, ym = y.copy(), y.copy()
+            yp[m] += h
+            ym[m] -= h
+            Jfd[:, m] = (net.rhs(yp, T, cvtot, None, **kw) - net.rhs(ym, T, cvtot, None, **kw)) / (2 * h)
+        s = np.maximum(np.abs(y), 1e-6 * np.abs(y).max())
+        Js, Fs = J * s[None, :], Jfd * s[None, :]
+        scale = np.maximum(np.abs(Js), np.abs(Fs)).max(axis=1, keepdims=True) + 1e-300
+        assert np.all(np.abs(Js - Fs) <= 1e-6 * scale), (wid, c)
+
+
+@pytest.mark.parametrize("wid", [7, 8])
+def test_tables_and_photo_conservation(oracle_mod, wid):
+    wl = I.workload(wid, 4)
+    netw = wl.network
+    r = oracle_mod.OracleNetwork(netw).integrate(wl.cells, wl.tol.dt, oracle_mod.options(wl.tol, scheme=1), 2)
+    assert np.all(r["status"] == 0)
+    y0 = np.maximum(wl.cells.y, 0.0)
+    b0, b1 = netw.counts.T @ y0, netw.counts.T @ r["y"]
+    assert np.all(np.abs(b1 - b0) <= 1e-12 * b0)
+    assert np.all(r["y"] >= 0.0)
