@@ -323,6 +323,55 @@ KT_API int kt_network_attach_mlp(kt_network *net, const kt_mlp *mlp);
  * library's table-driven exponential (valid for -708 <= x <= 709). */
 KT_API int kt_debug_exp(const double *x, double *out, int64_t n, int which, void *cuda_stream);
 
+/* Stoichiometry-compatible species advection, one directional sweep (Sec. 2.1.3,
+ * Eqs. method-flux-sp, method-plm-general, method-sto-plm-proj, method-sto-plm-recon):
+ * on nlines periodic lines of L >= 3 uniform cells of width dx, x^s = n^s / rho is
+ * reconstructed piecewise-linearly with the modified van Leer limiter (slope
+ * sgn(a) min(2|a||b|/(|a|+|b|), |b|) from the forward and backward differences a, b;
+ * zero at extrema), the corrections are projected onto the null space of the network's
+ * element matrix (project = 1; the element abundances of every interface state then
+ * equal the cell's), the upwind state by the sign of the mass flux gives the species
+ * fluxes F^s = x^s F^rho, and
+ *   n_out = alpha n_base + (1 - alpha) (n_in - dtdx (F_{j+1/2} - F_{j-1/2}))
+ * (n_base may be NULL: n_out = the plain update).  Device float64 arrays: n_in, n_base,
+ * n_out [n_species][nlines][L]; rho, mass_flux [nlines][L], mass_flux[j] at the interface
+ * j-1/2.  n_out must not alias n_in.  scratch: device buffer of kt_advect_scratch_bytes(),
+ * 16-B aligned, reused by the call (calls sharing it must be ordered on one stream).
+ * nlines <= 65535.  Asynchronous on stream. */
+KT_API int kt_advect_sweep(const kt_network *net, int64_t nlines, int64_t L, const double *n_in,
+                           const double *rho, const double *mass_flux, double dx, double dtdx,
+                           double alpha, const double *n_base, double *n_out, int project,
+                           void *scratch, void *cuda_stream);
+
+/* Bytes of device scratch one kt_advect_sweep call needs. */
+KT_API size_t kt_advect_scratch_bytes(void);
+
+/* Ray tracing on a Cartesian mesh with Beer-Lambert deposition (Sec. 3, Eqs. cart-dl,
+ * method-rad-equiv-flux, method-rt-abs).  The box [0, nx hx] x [0, ny hy] x [0, nz hz]
+ * holds nx*ny*nz cells; kappa [nbins][nx][ny][nz] is each cell's inverse absorption
+ * length per energy bin.  Ray q starts at origins[3q..3q+2] with unit direction
+ * dirs[3q..3q+2] and photon counts n0[q*nbins + b]; in every cell it crosses, over the
+ * length dl between its entry and exit (the nearest axis plane of Eq. cart-dl), it adds
+ * N dl/(dV dt) (1 - e^-tau)/tau to feff and N (1 - e^-tau) to absorbed (tau = kappa dl,
+ * both [nbins][nx][ny][nz], accumulated: the caller zeroes them) and leaves with
+ * N e^-tau; escaped [nrays][nbins] (may be NULL) receives what leaves the box.  Rays
+ * starting outside the box deposit nothing.  Accumulation uses FP64 atomics, so sums
+ * over rays crossing one cell are order-dependent at rounding level.  nbins <= 8.
+ * Device float64 arrays; asynchronous on stream. */
+KT_API int kt_raytrace(int nx, int ny, int nz, double hx, double hy, double hz, int nbins,
+                       const double *kappa, int64_t nrays, const double *origins, const double *dirs,
+                       const double *n0, double dt, double *feff, double *absorbed, double *escaped,
+                       void *cuda_stream);
+
+/* Rays of an isotropic point source (Eq. method-rt-ph-num): nrays directions on a
+ * Fibonacci lattice (z_k = 1 - (2k+1)/nrays, azimuth k pi (3 - sqrt 5)), each of solid
+ * angle 4 pi / nrays, carrying lum[b] dt / nrays photons per bin.  src (3) and lum
+ * (nbins <= 8) are host arrays; origins, dirs [nrays][3] and n0 [nrays][nbins] are
+ * device outputs.  Asynchronous on stream. */
+KT_API int kt_rays_point_source(const double *src, const double *lum, int nbins, double dt,
+                                int64_t nrays, double *origins, double *dirs, double *n0,
+                                void *cuda_stream);
+
 /* Diagnostics: peak probe of the FP64 (fp32 = 0) or FP32 (fp32 = 1) pipe, the
  * denominator of the library's roofline figures.  Launches `blocks` blocks (0: 8 per
  * SM) of 256 threads, each thread running 8 independent fused multiply-add chains for

@@ -752,7 +752,13 @@ static double err_norm(const ko_cell *c, const double *y, const double *y2, cons
  * where f_g and f_{n+1} follow from the stage equations (f_g = (y_g - y_n)/(d h) - f_n,
  * f_{n+1} = (y_{n+1} - r2)/(d h)).  Accept when the weighted RMS of est is <= 1; the next
  * step is h * min(facmax, max(0.2, 0.9 err^(-1/3))).  (Hosea and Shampine 1996 analyse
- * this pair; their stiff filter of the estimate is not applied.) */
+ * this pair; their stiff filter of the estimate is not applied.)
+ * f_n is f(y_n) evaluated only on a cell's first step; after an accepted step it is the
+ * stage relation's f_{n+1} of that step ("first same as last").  An evaluated f(y_n)
+ * enters est with the factor ~0.47 h, and for a component with rate constant k its
+ * rounding (a sum of large, nearly cancelling rates) is amplified by h k, which reaches
+ * 1e10 on stiff networks: the decision err <= 1 would then follow rounding noise.  The
+ * stage relation carries no such amplification (its error is the Newton tolerance). */
 typedef struct {
     double g, d, w1, w0, C, a0, a1, a2;
 } trbdf2_coef;
@@ -771,18 +777,15 @@ static trbdf2_coef trbdf2_coefficients(void)
     return k;
 }
 
-/* One TR-BDF2 step of size h from yn: y1 receives y_{n+1} and est the local error
- * estimate.  Returns 0, or -1 when a stage's Newton iteration fails. */
-static int trbdf2_step(ko_cell *c, const double *yn, double h, double *y1, double *est)
+/* One TR-BDF2 step of size h from yn with f0 = f_n: y1 receives y_{n+1}, est the local
+ * error estimate and f1 the stage relation's f_{n+1}.  Returns 0, or -1 when a stage's
+ * Newton iteration fails. */
+static int trbdf2_step(ko_cell *c, const double *yn, const double *f0, double h, double *y1, double *est,
+                       double *f1)
 {
-    const ko_net *n = c->n;
     const trbdf2_coef k = trbdf2_coefficients();
     int N = c->N, i;
-    double f0[KO_MAXN], r[KO_MAXN], yg[KO_MAXN];
-    double T = n->energy ? yn[n->ns] : c->T_iso;
-    if (!(T > 0.0)) return -1;
-    cell_rates(n, &c->rd, yn, T, c->k, c->dk);
-    rhs(n, yn, c->k, &c->hc, f0);
+    double r[KO_MAXN], yg[KO_MAXN];
     const double dh = k.d * h, inv = 1.0 / dh;
     for (i = 0; i < N; i++) r[i] = yn[i] + dh * f0[i];
     for (i = 0; i < N; i++) yg[i] = yn[i];
@@ -793,9 +796,20 @@ static int trbdf2_step(ko_cell *c, const double *yn, double h, double *y1, doubl
     const double ce = 2.0 * k.C * h;
     for (i = 0; i < N; i++) {
         double fg = (yg[i] - yn[i]) * inv - f0[i];
-        double f1 = (y1[i] - r[i]) * inv;
-        est[i] = ce * (k.a0 * f0[i] + k.a1 * fg + k.a2 * f1);
+        f1[i] = (y1[i] - r[i]) * inv;
+        est[i] = ce * (k.a0 * f0[i] + k.a1 * fg + k.a2 * f1[i]);
     }
+    return 0;
+}
+
+/* f(y) of the cell (rates at y's temperature); -1 for a non-positive temperature. */
+static int cell_rhs(ko_cell *c, const double *y, double *f)
+{
+    const ko_net *n = c->n;
+    double T = n->energy ? y[n->ns] : c->T_iso;
+    if (!(T > 0.0)) return -1;
+    cell_rates(n, &c->rd, y, T, c->k, c->dk);
+    rhs(n, y, c->k, &c->hc, f);
     return 0;
 }
 
@@ -816,22 +830,33 @@ static int advance_trbdf2(ko_cell *c, double *y, double dt, double h0, double fa
 {
     const ko_options *o = c->o;
     int N = c->N, i;
-    double y1[KO_MAXN], est[KO_MAXN];
+    double y1[KO_MAXN], est[KO_MAXN], f0[KO_MAXN], f1[KO_MAXN];
     double t = 0.0, h = h0;
-    int nacc = 0, natt = 0;
+    int nacc = 0, natt = 0, f0ok = 0;
     for (;;) {
         if (natt >= o->max_substeps) return ADV_FAIL;
         natt++;
         int last = 0;
         if (t + h >= dt * (1.0 - 1e-12)) { h = dt - t; last = 1; }
-        if (trbdf2_step(c, y, h, y1, est)) {
+        if (!f0ok) {
+            if (cell_rhs(c, y, f0)) {
+                h *= 0.5;
+                if (h < o->h_min) return ADV_FAIL;
+                continue;
+            }
+            f0ok = 1;
+        }
+        if (trbdf2_step(c, y, f0, h, y1, est, f1)) {
             h *= 0.5;
             if (h < o->h_min) return ADV_FAIL;
             continue;
         }
         double err = o->adaptive ? est_norm(c, y, y1, est) : 0.0;
         if (err <= 1.0) {
-            for (i = 0; i < N; i++) y[i] = y1[i];
+            for (i = 0; i < N; i++) {
+                y[i] = y1[i];
+                f0[i] = f1[i];          /* first same as last */
+            }
             nacc++;
             if (last) break;
             t += h;
@@ -1157,7 +1182,9 @@ int ko_trbdf2_step(const ko_net *n, const ko_options *o, const double *yn, doubl
     c->rd.flux = 1.0; c->rd.path = 0.0; c->rd.ltab = c->ltab;
     if (n->ntab) table_reduce(n, 1.0, c->ltab);
     c->atol_s = o->atol; c->nnewton = 0;
-    rc = trbdf2_step(c, yn, h, y_out, est_out);
+    double f0[KO_MAXN], f1[KO_MAXN];
+    rc = cell_rhs(c, yn, f0);
+    if (!rc) rc = trbdf2_step(c, yn, f0, h, y_out, est_out, f1);
     free(c);
     return rc;
 }

@@ -611,6 +611,46 @@ int integrate_impl(const kt_network *net, int64_t ncells, const double *y_in, co
 
 }  // namespace
 
+// Orthonormal basis of the row space of the element matrix N [n_elements][n_species]
+// (modified Gram-Schmidt, two passes per vector; rows whose remainder falls below
+// 1e-12 of their norm are dependent and dropped): Vr[s * rank + k].  P = I - Vr Vr^T is
+// the projector onto the stoichiometric space null(N) (Sec. 2.1.3).
+int kt::network_element_basis(const kt_network *net, double *Vr, int *ns_out, int *rank_out)
+{
+    if (!net) return fail(KT_EINVAL, "NULL network");
+    const int ns = net->ns, ne = net->ne;
+    if (ns > 256) return fail(KT_EUNSUPPORTED, "element basis: more than 256 species");
+    std::vector<std::vector<double>> basis;
+    for (int e = 0; e < ne; ++e) {
+        std::vector<double> v(ns);
+        double n0 = 0.0;
+        for (int s = 0; s < ns; ++s) {
+            v[s] = static_cast<double>(net->counts[s * ne + e]);
+            n0 += v[s] * v[s];
+        }
+        n0 = std::sqrt(n0);
+        if (!(n0 > 0.0)) continue;
+        for (int pass = 0; pass < 2; ++pass)
+            for (const auto &q : basis) {
+                double d = 0.0;
+                for (int s = 0; s < ns; ++s) d += q[s] * v[s];
+                for (int s = 0; s < ns; ++s) v[s] -= d * q[s];
+            }
+        double nn = 0.0;
+        for (int s = 0; s < ns; ++s) nn += v[s] * v[s];
+        nn = std::sqrt(nn);
+        if (!(nn > 1e-12 * n0)) continue;
+        for (int s = 0; s < ns; ++s) v[s] /= nn;
+        basis.push_back(v);
+    }
+    const int r = static_cast<int>(basis.size());
+    for (int s = 0; s < ns; ++s)
+        for (int k = 0; k < r; ++k) Vr[s * r + k] = basis[k][s];
+    *ns_out = ns;
+    *rank_out = r;
+    return KT_OK;
+}
+
 int kt::prepare_launch(const kt_network *net, int64_t ncells, const double *y_in, const double *T_in,
                        const double *rho, double dt, const kt_options *opts, double *y_out, double *T_out,
                        int32_t *status, int32_t *n_substeps, int32_t *n_newton, kt::LaunchArgs *a,

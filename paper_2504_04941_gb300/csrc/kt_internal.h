@@ -211,6 +211,9 @@ int prepare_launch(const kt_network *net, int64_t ncells, const double *y_in, co
                    int32_t *status, int32_t *n_substeps, int32_t *n_newton, LaunchArgs *a, LaunchCfg *c,
                    const unsigned char **host_blob);
 
+// Orthonormal basis Vr [ns][rank] of the element matrix's row space (rank <= 8).
+int network_element_basis(const kt_network *net, double *Vr, int *ns, int *rank);
+
 // Longest-first queue order from per-cell cost counts (kt_sched.cu): work holds
 // 2 * kSchedBuckets unsigned words, order receives a permutation of 0..ncells-1 with the
 // cells of the largest counts first.  Returns a cudaError_t value.

@@ -459,7 +459,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
 
     // TR-BDF2 (o.scheme == KT_SCHEME_TRBDF2, uniform over the launch): phase 0 is the
     // trapezoidal stage (iterate YF), phase 1 the BDF2 stage (iterate Y2); YH holds the
-    // stage's right-hand side r and FY the rate f(y_n) of the step's start state.
+    // stage's right-hand side r and FY the rate f_n of the step's start state: evaluated
+    // on the cell's first step, afterwards the previous step's stage relation
+    // f_{n+1} = (y_{n+1} - r)/(d h) (an evaluated f(y_n) would enter the error estimate
+    // multiplied by h, which turns its rounding into noise in err on stiff components).
     const bool TR = o.scheme == KT_SCHEME_TRBDF2;
     const TrCoef tr = tr_coef();
 
@@ -740,8 +743,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
         }
         const double err = sqrt(s2 / N);
         if (err <= 1.0) {
-            for (int i = 0; i < N; ++i) LI(Y, i) = LI(Y2, i);
-            fyok = false;
+            for (int i = 0; i < N; ++i) {
+                LI(FY, i) = (LI(Y2, i) - LI(YH, i)) * inv;   // first same as last
+                LI(Y, i) = LI(Y2, i);
+            }
+            fyok = true;
             jY = false;
             ++nacc;
             if (last) {
@@ -915,10 +921,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
             if (CVP) LI(M64, ns * N + ns) += hph * LI(W, ns) * dcvr;
             if (F32) jY = false;   // the FP64 matrix overlays the FP32 Jacobian
             if (trF0) {
-                for (int i = 0; i < N; ++i) {
-                    LI(FY, i) = LI(W, i);
-                    LI(YH, i) = LI(Y, i) + hph * LI(W, i);
+                if (!fyok) {
+                    for (int i = 0; i < N; ++i) LI(FY, i) = LI(W, i);
+                    fyok = true;
                 }
+                for (int i = 0; i < N; ++i) LI(YH, i) = LI(Y, i) + hph * LI(FY, i);
             }
             for (int i = 0; i < N; ++i) LI(W, i) = -(LI(yt, i) - LI(yb, i) - hph * LI(W, i));
             luok = crout_lu<double, 5>(M64, V64, P, N);
@@ -933,7 +940,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
                 else
                     reaction_pass<NT, ENERGY, 2, false>(nv, t, yt, K, lt, invT, invCVi, hph, W, nullptr, J32, doJ);
                 if (CVP && doJ) LIS(J32, ns * N + ns, 6) -= static_cast<float>(LI(W, ns) * dcvr);
-                if (atY) {
+                if (atY && !(TR && fyok)) {
                     for (int i = 0; i < N; ++i) LI(FY, i) = LI(W, i);
                     fyok = true;
                 }
@@ -960,7 +967,6 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
         // dmaxr = max |delta| / (newton_rtol |y|), the purely relative part
         float dmax = 0.0f, dmaxr = 0.0f;
         const double natol = (F32 ? natol_frac * kF32NewtonAtolScale : natol_frac) * atol_s;
-        const float natol_f = static_cast<float>(natol);
         for (int i = 0; i < N; ++i) {
             const double d = LI(W, i);
             const double y = LI(yt, i) + d;
@@ -970,7 +976,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
             if (F32) {
                 const float ad = static_cast<float>(fabs(d)), tf = static_cast<float>(tol);
                 const float q = __fdiv_rn(ad, fmaxf(tf, 1e-37f));
-                const float qr = __fdiv_rn(ad, fmaxf(i < ns ? tf - natol_f : tf, 1e-37f));
+                // the relative part newton_rtol |y| formed directly: as a difference
+                // tf - natol in FP32 it rounds to an ulp of natol for trace species
+                const float trl = static_cast<float>(o.newton_rtol * fabs(y));
+                const float qr = __fdiv_rn(ad, fmaxf(trl, 1e-37f));
                 dmax = q > dmax ? q : dmax;
                 dmaxr = qr > dmaxr ? qr : dmaxr;
             }

@@ -523,7 +523,6 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 2) warp_kernel(const LaunchArg
             // max |delta| / (newton_rtol |y|), the purely relative part of the tolerance
             float dmax = 0.0f, dmaxr = 0.0f;
             const double natol = (F32 ? o.newton_atol_frac * kF32NewtonAtolScale : o.newton_atol_frac) * atol_s;
-            const float natol_f = static_cast<float>(natol);
 #pragma unroll
             for (int q = 0; q < kQ; ++q) {
                 const int i = lane + 32 * q;
@@ -535,7 +534,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 2) warp_kernel(const LaunchArg
                     if (F32) {
                         const float ad = static_cast<float>(fabs(x[q])), tf = static_cast<float>(tol);
                         const float r = __fdiv_rn(ad, fmaxf(tf, 1e-37f));
-                        const float rr = __fdiv_rn(ad, fmaxf(i < ns ? tf - natol_f : tf, 1e-37f));
+                        // the relative part newton_rtol |y| formed directly: as a difference
+                        // tf - natol in FP32 it rounds to an ulp of natol for trace species
+                        const float trl = static_cast<float>(o.newton_rtol * fabs(y));
+                        const float rr = __fdiv_rn(ad, fmaxf(trl, 1e-37f));
                         dmax = r > dmax ? r : dmax;
                         dmaxr = rr > dmaxr ? rr : dmaxr;
                     }
@@ -581,9 +583,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 2) warp_kernel(const LaunchArg
     // call of be_solve below (one inlined copy of the solver per kernel).
     //   backward Euler with step doubling: stage 0 the full step h from Y (-> YF),
     //     stage 1 the first half step from Y (-> YH), stage 2 the second from YH (-> Y2)
-    //   TR-BDF2 (o.scheme == KT_SCHEME_TRBDF2): stage 0 trapezoidal, r = Y + d h f(Y) in
-    //     YH (-> YF), stage 1 BDF2, r = w1 YF - w0 Y in YH (-> Y2); F0 holds f(Y) and one
-    //     FP32 factor of I - d h J serves both stages
+    //   TR-BDF2 (o.scheme == KT_SCHEME_TRBDF2): stage 0 trapezoidal, r = Y + d h f_n in
+    //     YH (-> YF), stage 1 BDF2, r = w1 YF - w0 Y in YH (-> Y2); one FP32 factor of
+    //     I - d h J serves both stages.  F0 holds f_n: f(Y) on the cell's first step,
+    //     afterwards the previous step's stage relation (y_{n+1} - r)/(d h), which keeps
+    //     the rounding of an evaluated rate (amplified by h k in the error estimate) out
+    //     of the accept decision
     auto advance = [&](double h0, double fgrow, int &nacc) -> bool {
         const bool trs = o.scheme == KT_SCHEME_TRBDF2;
         const TrCoef tr = tr_coef();
@@ -672,9 +677,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 2) warp_kernel(const LaunchArg
             }
             const double err = sqrt(wsum(s2) / N);
             if (err <= 1.0) {
-                for (int i = lane; i < N; i += 32) Y[i] = Y2[i];
+                const double inv = trs ? 1.0 / dh : 0.0;
+                for (int i = lane; i < N; i += 32) {
+                    if (trs) F0[i] = (Y2[i] - YH[i]) * inv;    // first same as last
+                    Y[i] = Y2[i];
+                }
                 __syncwarp();
-                f0ok = false;
                 ++nacc;
                 if (last) return true;
                 tt += h;

@@ -79,6 +79,13 @@ def lib():
                                         ctypes.POINTER(Options), dptr, dptr, dptr, dptr, dptr,
                                         dptr, vp]
         L.kt_scratch_check.argtypes = [vp, vp]
+        L.kt_advect_sweep.argtypes = [vp, c_i64, c_i64, dptr, dptr, dptr, ctypes.c_double, ctypes.c_double,
+                                      ctypes.c_double, dptr, dptr, c_int, vp, vp]
+        L.kt_advect_scratch_bytes.restype = ctypes.c_size_t
+        L.kt_raytrace.argtypes = [c_int, c_int, c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double, c_int,
+                                  dptr, c_i64, dptr, dptr, dptr, ctypes.c_double, dptr, dptr, dptr, vp]
+        L.kt_rays_point_source.argtypes = [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), c_int,
+                                           ctypes.c_double, c_i64, dptr, dptr, dptr, vp]
         L.kt_integrate_rad.argtypes = [vp, c_i64, dptr, dptr, dptr, dptr, dptr, ctypes.c_double,
                                        ctypes.POINTER(Options), dptr, dptr, dptr, dptr, dptr, vp, vp]
         L.kt_integrate_dt.argtypes = [vp, c_i64, dptr, dptr, dptr, dptr, ctypes.POINTER(Options),
@@ -525,6 +532,69 @@ def debug_exp(x, which: int, stream=None):
     out = torch.empty_like(x)
     _check(lib().kt_debug_exp(_ptr(x), _ptr(out), x.numel(), int(which), _stream_handle(stream)))
     return out
+
+
+def advect_sweep(net: Network, n, rho, mass_flux, dx: float, dtdx: float, alpha: float = 0.0,
+                 n_base=None, out=None, project: bool = True, scratch=None, stream=None):
+    """kt_advect_sweep: one stoichiometry-compatible PLM sweep (Sec. 2.1.3) on periodic
+    lines.  n [n_species, n_lines, L], rho and mass_flux [n_lines, L] (mass_flux[:, j]
+    at the interface j-1/2), CUDA float64; returns n - dtdx (F_{j+1/2} - F_{j-1/2}),
+    blended as alpha * n_base + (1 - alpha) * (...) when n_base is given."""
+    import torch
+    ns, nl, L = (int(v) for v in n.shape)
+    if ns != net.ns:
+        raise ValueError(f"n has {ns} species, the network {net.ns}")
+    _require(n, "n", (ns, nl, L), "float64")
+    _require(rho, "rho", (nl, L), "float64")
+    _require(mass_flux, "mass_flux", (nl, L), "float64")
+    _require(n_base, "n_base", (ns, nl, L), "float64", optional=True)
+    if out is None:
+        out = torch.empty_like(n)
+    _require(out, "out", (ns, nl, L), "float64")
+    if scratch is None:
+        scratch = torch.empty(int(lib().kt_advect_scratch_bytes()), dtype=torch.uint8, device=n.device)
+    _check(lib().kt_advect_sweep(net.ptr, nl, L, _ptr(n), _ptr(rho), _ptr(mass_flux), float(dx), float(dtdx),
+                                 float(alpha), _ptr(n_base), _ptr(out), int(bool(project)), _ptr(scratch),
+                                 _stream_handle(stream)))
+    return out
+
+
+def advect_ssprk2(net: Network, n, rho, mass_flux, dx: float, dtdx: float, project: bool = True, stream=None):
+    """Two-stage SSP Runge-Kutta step of the sweep (both stages in the library's kernel)."""
+    n1 = advect_sweep(net, n, rho, mass_flux, dx, dtdx, project=project, stream=stream)
+    return advect_sweep(net, n1, rho, mass_flux, dx, dtdx, alpha=0.5, n_base=n, project=project, stream=stream)
+
+
+def point_source_rays(src, lum, dt: float, nrays: int, device="cuda", stream=None):
+    """kt_rays_point_source: (origins, dirs, n0) CUDA tensors of an isotropic source."""
+    import torch
+    lum = [float(v) for v in np.atleast_1d(lum)]
+    org = torch.empty((nrays, 3), dtype=torch.float64, device=device)
+    dirs = torch.empty((nrays, 3), dtype=torch.float64, device=device)
+    n0 = torch.empty((nrays, len(lum)), dtype=torch.float64, device=device)
+    s = (ctypes.c_double * 3)(*[float(v) for v in src])
+    l = (ctypes.c_double * len(lum))(*lum)
+    _check(lib().kt_rays_point_source(s, l, len(lum), float(dt), int(nrays), _ptr(org), _ptr(dirs), _ptr(n0),
+                                      _stream_handle(stream)))
+    return org, dirs, n0
+
+
+def raytrace(spacing, kappa, origins, dirs, n0, dt: float, stream=None):
+    """kt_raytrace: kappa [nbins, nx, ny, nz] CUDA float64; returns (feff, absorbed,
+    escaped) with the first two [nbins, nx, ny, nz] and escaped [nrays, nbins]."""
+    import torch
+    nb, nx, ny, nz = (int(v) for v in kappa.shape)
+    nr = int(origins.shape[0])
+    _require(kappa, "kappa", (nb, nx, ny, nz), "float64")
+    for t, nm, sh in ((origins, "origins", (nr, 3)), (dirs, "dirs", (nr, 3)), (n0, "n0", (nr, nb))):
+        _require(t, nm, sh, "float64")
+    feff = torch.zeros_like(kappa)
+    absorbed = torch.zeros_like(kappa)
+    escaped = torch.empty((nr, nb), dtype=torch.float64, device=kappa.device)
+    hx, hy, hz = (float(v) for v in spacing)
+    _check(lib().kt_raytrace(nx, ny, nz, hx, hy, hz, nb, _ptr(kappa), nr, _ptr(origins), _ptr(dirs), _ptr(n0),
+                             float(dt), _ptr(feff), _ptr(absorbed), _ptr(escaped), _stream_handle(stream)))
+    return feff, absorbed, escaped
 
 
 def fma_peak(fp32: bool, seconds: float = 0.5, repeats: int = 3) -> float:

@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 from paper_2504_04941_gb300 import inputs as I
-from _parity import compare, conservation_error, tight_oracle
+from _parity import atol_cells, compare, conservation_error, tight_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -114,7 +114,8 @@ def test_ism_ragged_parity(kt, oracle_mod, form):
     g = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, kt.options(wl.tol, form=form, persistent=1))
     o = ora_run(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol)
     rep = compare(g, o, wl.network.energy, rtol=wl.tol.rtol,
-                  tight=tight_oracle(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol, NTHREADS))
+                  tight=tight_oracle(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol, NTHREADS),
+                  atol_cells=atol_cells(wl.network, wl.cells, wl.tol))
     print(rep)
     assert rep.ok(), rep
     assert conservation_error(wl.network, wl.cells.y, g["y"]) <= 1e-12
@@ -157,7 +158,8 @@ def test_trbdf2_parity(kt, oracle_mod, wid, n, form):
     g = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, kt.options(wl.tol, scheme=1, **form))
     o = ora_run(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol, scheme=1)
     rep = compare(g, o, wl.network.energy, rtol=wl.tol.rtol,
-                  tight=tight_oracle(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol, NTHREADS, scheme=1))
+                  tight=tight_oracle(oracle_mod, wl.network, wl.cells, wl.tol.dt, wl.tol, NTHREADS, scheme=1),
+                  atol_cells=atol_cells(wl.network, wl.cells, wl.tol))
     print(rep)
     assert rep.ok(), rep
     assert conservation_error(wl.network, wl.cells.y, g["y"]) <= 1e-12
@@ -303,7 +305,8 @@ def test_tabulated_and_photo_rates_parity(kt, oracle_mod, wid, n, form):
     g = {k: r[k].cpu().numpy() for k in ("y", "T", "status", "nsub", "nnewton")}
     o = ora_run(oracle_mod, wl.network, c, wl.tol.dt, wl.tol, scheme=form["scheme"])
     rep = compare(g, o, wl.network.energy, rtol=wl.tol.rtol,
-                  tight=tight_oracle(oracle_mod, wl.network, c, wl.tol.dt, wl.tol, NTHREADS, scheme=form["scheme"]))
+                  tight=tight_oracle(oracle_mod, wl.network, c, wl.tol.dt, wl.tol, NTHREADS, scheme=form["scheme"]),
+                  atol_cells=atol_cells(wl.network, c, wl.tol))
     print(rep)
     assert rep.ok(), rep
     assert conservation_error(wl.network, c.y, g["y"]) <= 1e-12

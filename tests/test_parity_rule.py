@@ -45,3 +45,25 @@ def test_identical_runs_pass(oracle_mod):
     ora = _run(oracle_mod, wl)
     rep = compare(ora, ora, 1)
     assert rep.ok() and rep.n_flip == 0 and rep.max_rel_y == 0.0
+
+
+def test_species_below_atol_compared_absolutely(oracle_mod):
+    """On a density-scaled-atol network a species below the cell's atol is held to
+    1e-6 atol absolutely; above it the relative 1e-6 rule applies."""
+    from _parity import atol_cells
+    wl = I.workload(3, 2)
+    ora = _run(oracle_mod, wl)
+    at = atol_cells(wl.network, wl.cells, wl.tol)
+    assert at is not None and np.all(at > 1e-20)
+    g = {k: np.array(v, copy=True) for k, v in ora.items()}
+    s, c = np.unravel_index(np.argmin(np.where(ora["y"] > 1e-20, ora["y"], np.inf)), ora["y"].shape)
+    assert ora["y"][s, c] < at[c]
+    g["y"][s, c] += 0.5e-6 * at[c]                       # inside the absolute allowance
+    assert compare(g, ora, 0, atol_cells=at).ok()
+    assert not compare(g, ora, 0).ok()                    # the plain relative rule rejects it
+    g["y"][s, c] += 2e-6 * at[c]
+    assert not compare(g, ora, 0, atol_cells=at).ok()
+    big = np.argmax(ora["y"][:, c])
+    g = {k: np.array(v, copy=True) for k, v in ora.items()}
+    g["y"][big, c] *= 1 + 2e-6
+    assert not compare(g, ora, 0, atol_cells=at).ok()
