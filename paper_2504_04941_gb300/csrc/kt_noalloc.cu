@@ -63,6 +63,12 @@ extern "C" KT_API int kt_integrate_noalloc(const kt_network *net, int64_t ncells
                                            int32_t *status, int32_t *n_substeps, int32_t *n_newton,
                                            void *cuda_stream)
 {
+    // the per-cell status is this call's only report of a device-side failure (the error
+    // word sits in the internal array, which the caller cannot read), so it is required
+    if (!status) {
+        kt::set_error("kt_integrate_noalloc: status must not be NULL (it is the only error report)");
+        return KT_EINVAL;
+    }
     kt::LaunchArgs a{};
     kt::LaunchCfg c{};
     const unsigned char *host_tables = nullptr;
@@ -90,7 +96,7 @@ extern "C" KT_API int kt_integrate_noalloc(const kt_network *net, int64_t ncells
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(area + kTablesOffset, host_tables, static_cast<size_t>(a.nv.bytes_total),
                             cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && status) e = cudaMemsetAsync(status, 0xff, static_cast<size_t>(ncells) * sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0xff, static_cast<size_t>(ncells) * sizeof(int32_t), s);
     if (e != cudaSuccess) {
         char msg[256];
         std::snprintf(msg, sizeof msg, "kt_integrate_noalloc: %s", cudaGetErrorString(e));

@@ -53,6 +53,21 @@ def test_no_alloc_matches_allocating_entry_point(kt, wid, n, dt_scale, form):
         assert compare(got, ref, wl.network.energy, rtol=wl.tol.rtol).ok(), (wid, call)
         for k in ref:
             assert np.array_equal(got[k], ref[k]), (wid, call, k)
+        assert np.all(got["status"] == 0), (wid, call)   # every cell reached, none failed
+
+
+def test_no_alloc_requires_status(kt):
+    # status is the call's only report of a device-side failure, so NULL is refused
+    import torch
+    wl = I.workload(1, 8)
+    net = kt.Network(wl.network)
+    y = torch.from_numpy(wl.cells.y).cuda()
+    T = torch.from_numpy(wl.cells.T).cuda()
+    out = _outputs(y, T)
+    del out["status"]
+    with pytest.raises(kt.KtError) as ei:
+        kt.integrate_noalloc(net, y, T, 1.0, kt.options(wl.tol), out)
+    assert ei.value.code == -1 and "status" in str(ei.value)
 
 
 def test_no_alloc_refuses_networks_beyond_its_area(kt):
