@@ -37,11 +37,15 @@ def _features(y, T, rho, h):
     return X
 
 
-def _targets(y0, y1):
+def _targets(y0, y1, T0=None, T1=None):
+    """[n, 16] change of log max(y, floor) over the step (and of log T with the energy
+    equation)."""
     import torch
     ns, n = y0.shape
     D = torch.zeros((n, kt.MLP_OUT), dtype=torch.float64, device=y0.device)
     D[:, :ns] = (torch.log(torch.clamp(y1, min=FLOOR)) - torch.log(torch.clamp(y0, min=FLOOR))).T
+    if T0 is not None:
+        D[:, ns] = torch.log(T1) - torch.log(T0)
     return D
 
 
@@ -86,7 +90,7 @@ def make_pairs(net: kt.Network, wl: I.Workload, n_pairs: int, seed: int,
 
 def normalisation(pairs):
     X = _features(pairs["y0"], pairs["T"], pairs["rho"], pairs["dt"])
-    D = _targets(pairs["y0"], pairs["y1"])
+    D = _targets(pairs["y0"], pairs["y1"], pairs.get("T"), pairs.get("T1"))
     mu_in, sd_in = X.mean(0), X.std(0)
     mu_out, sd_out = D.mean(0), D.std(0)
     sd_in = torch_where_small(sd_in)
@@ -103,17 +107,52 @@ def normalised_tensors(pairs, norm):
     import torch
     mu_in, sd_in, mu_out, sd_out = (torch.from_numpy(np.asarray(v, np.float64)).cuda() for v in norm)
     X = (_features(pairs["y0"], pairs["T"], pairs["rho"], pairs["dt"]) - mu_in) / sd_in
-    D = (_targets(pairs["y0"], pairs["y1"]) - mu_out) / sd_out
+    D = (_targets(pairs["y0"], pairs["y1"], pairs.get("T"), pairs.get("T1")) - mu_out) / sd_out
     return X.float().contiguous(), D.float().contiguous()
+
+
+def combustion_pairs(net: kt.Network, wl: I.Workload, n_pairs: int, seed: int,
+                     h_range=(1e-12, 1e-8), n_snap: int = 40) -> Dict[str, "object"]:
+    """Solver-generated pairs on a network with the energy equation (the combustion
+    workload): cells of the workload's distribution advanced along their trajectories
+    (snapshots at log-spaced times from 1e-11 s to the workload's dt, T and density
+    per cell), each snapshot paired with a step h ~ log-uniform(h_range) (the sub-step
+    sizes of that workload) and the solver's end state after h."""
+    import torch
+    n_traj = max(1, -(-n_pairs // n_snap))
+    cells = I.combustion_cells(wl.network, n_traj, seed)
+    y = torch.from_numpy(cells.y).cuda()
+    T = torch.from_numpy(cells.T).cuda()
+    rho = torch.from_numpy(cells.rho).cuda()
+    opts = kt.options(wl.tol, form=kt.KT_FORM_FP32LU, persistent=1, scheme=kt.KT_SCHEME_TRBDF2)
+    ys, Ts, prev = [], [], 0.0
+    for tk in np.geomspace(1e-11, wl.tol.dt, n_snap):
+        r = kt.integrate(net, y, T, float(tk - prev), opts, rho=rho)
+        kt.check_scratch(r["scratch"])
+        y, T = r["y"], r["T"]
+        ys.append(y.clone())
+        Ts.append(T.clone())
+        prev = tk
+    y0 = torch.cat(ys, dim=1)[:, :n_pairs].contiguous()
+    T0 = torch.cat(Ts)[:n_pairs].contiguous()
+    rho0 = rho.repeat(n_snap)[:n_pairs].contiguous()
+    g = torch.Generator(device="cpu").manual_seed(seed + 1)
+    u = torch.rand(T0.shape[0], generator=g, dtype=torch.float64)
+    h = torch.exp(math.log(h_range[0]) + u * (math.log(h_range[1]) - math.log(h_range[0]))).cuda()
+    r = kt.integrate_dt(net, y0, T0, h, kt.options(wl.tol, persistent=1, scheme=kt.KT_SCHEME_TRBDF2),
+                        rho=rho0)
+    kt.check_scratch(r["scratch"])
+    ok = r["status"] == 0
+    return dict(y0=y0[:, ok], T=T0[ok], rho=rho0[ok], dt=h[ok], y1=r["y"][:, ok], T1=r["T"][ok])
 
 
 def train(net: kt.Network, wl: I.Workload, n_pairs: int = 1_000_000, epochs: int = 4,
           batch: int = 4096, lr: float = 2e-3, seed: int = 2504, val_pairs: int = 65536,
-          log=print) -> Dict[str, object]:
+          log=print, pairs_fn=None) -> Dict[str, object]:
     """Generate pairs with the solver and train a fresh MLP; returns the MLP and stats."""
     import torch
     t0 = time.perf_counter()
-    pairs = make_pairs(net, wl, n_pairs + val_pairs, seed)
+    pairs = (pairs_fn or make_pairs)(net, wl, n_pairs + val_pairs, seed)
     t_data = time.perf_counter() - t0
     n = pairs["T"].shape[0]
     norm = normalisation({k: v[..., :n - val_pairs] for k, v in pairs.items()})
@@ -150,6 +189,9 @@ def train(net: kt.Network, wl: I.Workload, n_pairs: int = 1_000_000, epochs: int
     rel = torch.expm1((dlog_pred - dlog_true).abs()).max(dim=1).values
     y0v = pairs["y0"][:, n - val_pairs:]
     y1v = pairs["y1"][:, n - val_pairs:]
+    if net.energy:
+        y0v = torch.cat([y0v, pairs["T"][None, n - val_pairs:]])
+        y1v = torch.cat([y1v, pairs["T1"][None, n - val_pairs:]])
     plain = ((y1v - y0v).abs() / torch.clamp(y1v.abs(), min=1e-300)).max(dim=0).values
     return dict(mlp=mlp, norm=norm, val_loss=val, losses=losses, steps=k,
                 seconds_data=t_data, seconds_train=t_train, pairs=ntr,
@@ -219,6 +261,64 @@ def study(n_pairs: int, n_cells: int, epochs: int, seed: int = 2504, log=print) 
     return out
 
 
+def combustion_study(n_pairs: int = 1_000_000, n_cells: int = 65536, epochs: int = 3,
+                     dt_scale: float = 0.1, seed: int = 2504, log=print,
+                     arrays: bool = False) -> Dict[str, object]:
+    """The learned guess on the benchmark's combustion network (10 species + T): train on
+    solver-generated pairs, then integrate the benchmark batch's first n_cells cells over
+    dt_scale x its interval in the FP32-LU persistent form under backward Euler (the
+    scheme the learned start serves) with the plain and the learned starting point, and
+    report Newton iterations, cells/s of each and the largest relative change of the
+    answer (the solver's converged result decides, so it must stay at the Newton
+    tolerance's level)."""
+    import torch
+    wl = I.workload(2, n_cells)
+    net = kt.Network(wl.network)
+    st = train(net, wl, n_pairs=n_pairs, epochs=epochs, seed=seed, log=log, pairs_fn=combustion_pairs)
+    dt = wl.tol.dt * dt_scale
+    y = torch.from_numpy(wl.cells.y).cuda()
+    T = torch.from_numpy(wl.cells.T).cuda()
+    rho = torch.from_numpy(wl.cells.rho).cuda()
+    st["mlp"].attach(net)
+    res = {}
+    for name, guess in (("plain", kt.KT_GUESS_PREV), ("mlp", kt.KT_GUESS_MLP)):
+        opts = kt.options(wl.tol, form=kt.KT_FORM_FP32LU, persistent=1, scheme=kt.KT_SCHEME_BE, guess=guess)
+        kt.integrate(net, y, T, dt, opts, rho=rho)                     # warm-up
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        r = kt.integrate(net, y, T, dt, opts, rho=rho)
+        b.record()
+        kt.check_scratch(r["scratch"])
+        torch.cuda.synchronize()
+        res[name] = dict(ms=a.elapsed_time(b), y=r["y"].cpu().numpy(), T=r["T"].cpu().numpy(),
+                         status=r["status"].cpu().numpy(), nnewton=r["nnewton"].cpu().numpy(),
+                         nsub=r["nsub"].cpu().numpy())
+    p, m = res["plain"], res["mlp"]
+    big = p["y"] > 1e-20
+    relm = np.where(big, np.abs(m["y"] - p["y"]) / np.where(big, p["y"], 1.0), 0.0)
+    rel = relm[big]
+    out = {"workload": f"{wl.name}: {wl.network.ns} species + T, first {n_cells} cells of the benchmark "
+                        f"batch over dt={dt:g} s, backward Euler, FP32-LU, persistent",
+            "pairs": st["pairs"], "train_steps": st["steps"], "val_loss": st["val_loss"],
+            "seconds_data": st["seconds_data"], "seconds_train": st["seconds_train"],
+            "guess_rel_err_median": st["guess_rel_err_median"],
+            "plain_rel_err_median": st["plain_rel_err_median"],
+            "newton_plain": int(p["nnewton"].sum()), "newton_mlp": int(m["nnewton"].sum()),
+            "newton_saved_frac": float(1.0 - m["nnewton"].sum() / p["nnewton"].sum()),
+            "ms_plain": p["ms"], "ms_mlp": m["ms"],
+            "cells_per_s_plain": n_cells / (p["ms"] * 1e-3), "cells_per_s_mlp": n_cells / (m["ms"] * 1e-3),
+            "status_ok_plain": int((p["status"] == 0).sum()), "status_ok_mlp": int((m["status"] == 0).sum()),
+            "max_rel_change_of_answer": float(rel.max(initial=0.0)),
+            # a different start can flip an accept decision of the step control; such
+            # cells follow another valid step sequence and differ at the scheme's accuracy
+            "cells_changed_over_1e-6": int((relm > 1e-6).any(axis=0).sum()),
+            "max_rel_change_of_T": float((np.abs(m["T"] - p["T"]) / p["T"]).max(initial=0.0))}
+    if arrays:
+        out["mlp_result"] = {k: m[k] for k in ("y", "T", "status", "nsub", "nnewton")}
+    return out
+
+
 if __name__ == "__main__":
     import argparse
     import json
@@ -226,5 +326,11 @@ if __name__ == "__main__":
     ap.add_argument("--pairs", type=int, default=10_000_000)
     ap.add_argument("--cells", type=int, default=262_144)
     ap.add_argument("--epochs", type=int, default=2)
+    ap.add_argument("--combustion", action="store_true",
+                    help="the study on the combustion network instead (combustion_study)")
     a = ap.parse_args()
-    print(json.dumps(study(a.pairs, a.cells, a.epochs, log=lambda *x: None)), flush=True)
+    if a.combustion:
+        out = combustion_study(a.pairs, a.cells, a.epochs, log=lambda *x: None)
+    else:
+        out = study(a.pairs, a.cells, a.epochs, log=lambda *x: None)
+    print(json.dumps(out), flush=True)

@@ -4,6 +4,8 @@ Forward and gradients use BF16 weights and BF16 activations with FP32 accumulati
 so they are compared with the FP64 reference evaluated on the same BF16-rounded
 weights and inputs, per tensor: relative L2 error <= 3e-2 and cosine >= 0.999.
 """
+import json
+import math
 import os
 
 import numpy as np
@@ -169,3 +171,29 @@ def test_trained_guess_saves_newton_iterations(kt, oracle_mod):
         big = o["y"][:, 0] > 1e-20
         rel = np.abs(mlp["y"][:, i] - o["y"][:, 0])[big] / o["y"][big, 0]
         assert rel.max() <= 1e-6, (i, rel.max())
+
+
+def test_learned_guess_on_the_combustion_network(kt, oracle_mod):
+    """The learned start on the benchmark's network (10 species + T), trained by the
+    library's kernels on solver-generated pairs: the answer stays the solver's, and the
+    test reports what the guess does to the Newton iterations and to cells/s of the
+    FP32-LU persistent form under backward Euler (a measurement: the benchmark's chosen
+    form runs TR-BDF2 without it)."""
+    from paper_2504_04941_gb300 import guess
+    n = 8192
+    out = guess.combustion_study(n_pairs=200_000, n_cells=n, epochs=2, dt_scale=0.01, log=lambda *a: None,
+                                 arrays=True)
+    res = out.pop("mlp_result")
+    print(json.dumps(out))
+    assert out["status_ok_plain"] == n and out["status_ok_mlp"] == n
+    assert out["cells_changed_over_1e-6"] <= n // 100, out["cells_changed_over_1e-6"]
+    assert math.isfinite(out["newton_saved_frac"]) and out["cells_per_s_mlp"] > 0 and out["cells_per_s_plain"] > 0
+    # the learned start's answer against the oracle on a sample of the cells
+    wl = I.workload(2, n)
+    idx = np.arange(0, n, 512)
+    sub = wl.cells.subset(idx)
+    g = {k: (v[:, idx] if v.ndim == 2 else v[idx]) for k, v in res.items()}
+    o = oracle_mod.OracleNetwork(wl.network).integrate(sub, wl.tol.dt * 0.01, oracle_mod.options(wl.tol),
+                                                       os.cpu_count())
+    assert compare(g, o, 1, tight=tight_oracle(oracle_mod, wl.network, sub, wl.tol.dt * 0.01, wl.tol,
+                                               os.cpu_count())).ok()
