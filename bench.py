@@ -289,6 +289,10 @@ def main():
                     help="scale the workload's dt (profiling captures on a short interval)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--lane-variant", type=int, default=None,
+                    help="fix the FP32-LU lane kernels' storage variant (kt.h KT_LANE_*) instead of tuning it")
+    ap.add_argument("--block-warps", type=int, default=None,
+                    help="fix the warps per block of the chosen form instead of tuning it")
     ap.add_argument("--cpu-cells", type=int, default=1024)
     ap.add_argument("--ref-cells", type=int, default=4096)
     args = ap.parse_args()
@@ -332,12 +336,17 @@ def main():
         base = kt.options(wl.tol, **forms["chosen"])
         # launch-shape cache (per network size, form and GPU name)
         cache = os.environ.get("KT_TUNE_CACHE", os.path.join(ROOT, ".tuned.json"))
-        # tune the launch shape on the whole batch over a short interval (dt/1000): every
-        # candidate runs at full occupancy in well under a second
-        topts, tuned = kt.tuned_options(net, y_in, T_in, wl.tol.dt * 1e-3, base, cache,
+        # tune the launch shape on the whole batch over a tenth of the interval: every
+        # candidate runs at full occupancy with each cell past its first sub-steps (much
+        # shorter intervals favour the variant that is cheapest to start a cell with)
+        topts, tuned = kt.tuned_options(net, y_in, T_in, wl.tol.dt * 0.1, base, cache,
                                         sample=ncells)
-        for f in ("cells_per_warp", "persistent", "block_warps", "blocks_per_sm"):
+        for f in ("cells_per_warp", "persistent", "block_warps", "blocks_per_sm", "lane_variant"):
             forms["chosen"][f] = int(getattr(topts, f))
+    if args.lane_variant is not None:
+        forms["chosen"]["lane_variant"] = args.lane_variant
+    if args.block_warps is not None:
+        forms["chosen"]["block_warps"] = args.block_warps
     state = kt.State(net, ncells)
     zero_cost = torch.zeros(ncells, dtype=torch.int32, device=dev)
     results = {}

@@ -78,6 +78,18 @@ extern "C" {
                                order.  The second stage starts from the first stage's
                                result whatever `guess` says; KT_GUESS_MLP is refused. */
 
+/* storage of the FP32-LU lane-per-cell kernels under TR-BDF2 (kt_options.lane_variant) */
+#define KT_LANE_AUTO 0      /* KT_LANE_LEAN where it applies */
+#define KT_LANE_JCACHE 1    /* the FP32 Jacobian is kept beside the iteration matrix (a
+                               rejected attempt re-uses it) and a failed FP32 solve is
+                               redone in FP64 Newton from its start before h halves;
+                               52 KB of shared memory per warp for 11 unknowns */
+#define KT_LANE_LEAN 2      /* the iteration matrix I - d h J is assembled directly in
+                               FP32 (no Jacobian copy), the step's start state and rate
+                               stay in registers, and a failed FP32 solve halves h (no
+                               FP64 rescue); 27 KB per warp for 11 unknowns, so twice as
+                               many warps share an SM */
+
 typedef struct kt_network kt_network;
 typedef struct kt_state kt_state;
 typedef struct kt_mlp kt_mlp;
@@ -121,7 +133,9 @@ typedef struct {
                                 zero after kt_state_create), 0 in index order.  The
                                 order changes no result, only the load balance (0) */
     int scheme;              /* KT_SCHEME_*: the one-step scheme of each sub-step      (BE) */
-    int reserved[3];
+    int lane_variant;        /* KT_LANE_*: storage of the FP32-LU lane-per-cell kernels
+                                with TR-BDF2 (3 or 11 unknowns); ignored elsewhere (AUTO) */
+    int reserved[2];
 } kt_options;
 
 /* Defaults listed above. */
@@ -252,8 +266,11 @@ KT_API int kt_integrate_dt(const kt_network *net, int64_t ncells, const double *
  * counter and refreshes the tables itself; calls that overlap on the GPU (two streams,
  * two host threads) race on it and must be ordered by the caller.  Same arguments and
  * buffer rules as kt_integrate_ptrs except the scratch, which is internal; the
- * learned guess is not available here (KT_EUNSUPPORTED).  Cells the kernels did not
- * reach because of a device error keep status -1. */
+ * learned guess is not available here (KT_EUNSUPPORTED).  Each call copies the network
+ * tables from host memory into the array on cuda_stream.  status is required (NULL is
+ * KT_EINVAL): it is the call's only report of a device-side failure, since the device
+ * error word sits in the internal array; cells the kernels did not reach because of a
+ * device error keep status -1. */
 KT_API int kt_integrate_noalloc(const kt_network *net, int64_t ncells, const double *y_in,
                                 const double *T_in, const double *rho, double dt,
                                 const kt_options *opts, double *y_out, double *T_out,

@@ -312,7 +312,6 @@ void build_blob(kt_network *n)
     v.off_A = o; o = align16(o + 8 * n->nr);
     v.off_b = o; o = align16(o + 8 * n->nr);
     v.off_th = o; o = align16(o + 8 * n->nr);
-    v.off_dH = o; o = align16(o + 8 * n->nr);
     v.off_h = o; o = align16(o + 8 * n->ns);
     v.off_cv = o; o = align16(o + 8 * n->ns);
     v.off_cnt = o; o = align16(o + 8 * n->ns * n->ne);
@@ -351,6 +350,12 @@ void build_blob(kt_network *n)
     v.off_rtype = o; o = align16(o + 4 * n->nr);
     v.off_sigr = o; o = align16(o + 8 * n->nr);
     v.off_sigs = o; o = align16(o + 8 * n->ns);
+    // the warp kernels stage the prefix up to here (the photo and table descriptors
+    // only for networks that have such rates); the reaction heats serve the lane kernels
+    v.bytes_warp = v.special ? o : v.off_rtype;
+    v.off_dH = o; o = align16(o + 8 * n->nr);
+    // FP32 copies of b, theta and the heats for the FP32 Jacobian of the lane kernels
+    v.off_f32 = o; o = align16(o + 3 * 4 * n->nr);
     v.ntab = n->ntab;
     v.tab_nT = n->tab_nT;
     v.tab_nR = n->tab_nR;
@@ -375,6 +380,9 @@ void build_blob(kt_network *n)
         for (int j = 0; j < n->nout[r]; ++j) dH += n->h[n->out[r][j]];
         for (int j = 0; j < n->nin[r]; ++j) dH -= n->h[n->in[r][j]];
         put(v.off_dH, r, dH);
+        const float f3[3] = {static_cast<float>(n->b[r]), static_cast<float>(n->th[r]), static_cast<float>(dH)};
+        for (int q = 0; q < 3; ++q)
+            std::memcpy(n->blob.data() + v.off_f32 + 4 * (q * n->nr + r), &f3[q], 4);
         unsigned char *ix = n->blob.data() + v.off_idx + 8 * r;
         bool distinct = true;   // no species twice among the reaction's reactants and products
         for (int a = 0; a < n->nin[r] + n->nout[r]; ++a)
@@ -417,7 +425,8 @@ int check_opts(const kt_options *o)
         o->max_newton < 1 || (o->form != KT_FORM_FP64 && o->form != KT_FORM_FP32LU) ||
         (o->guess != KT_GUESS_PREV && o->guess != KT_GUESS_MLP && o->guess != KT_GUESS_FULLSTEP) ||
         o->block_warps < 0 ||
-        o->blocks_per_sm < 0 || (o->scheme != KT_SCHEME_BE && o->scheme != KT_SCHEME_TRBDF2))
+        o->blocks_per_sm < 0 || (o->scheme != KT_SCHEME_BE && o->scheme != KT_SCHEME_TRBDF2) ||
+        o->lane_variant < KT_LANE_AUTO || o->lane_variant > KT_LANE_LEAN)
         return fail(KT_EINVAL, "options: a field is out of range");
     if (o->scheme == KT_SCHEME_TRBDF2 && o->guess == KT_GUESS_MLP)
         return fail(KT_EINVAL, "options: the learned guess needs scheme KT_SCHEME_BE");
@@ -603,7 +612,7 @@ int integrate_impl(const kt_network *net, int64_t ncells, const double *y_in, co
     a.nnew = n_newton;
     a.scratch = static_cast<kt::Scratch *>(scratch);
     a.order = opts->persistent ? order : nullptr;
-    kt::LaunchCfg c{opts->form, opts->persistent, opts->block_warps, opts->blocks_per_sm, cpw};
+    kt::LaunchCfg c{opts->form, opts->persistent, opts->block_warps, opts->blocks_per_sm, cpw, opts->lane_variant};
     int ce = cpw == 32 ? kt::launch_lane(a, c, cuda_stream) : kt::launch_warp(a, c, cuda_stream);
     if (ce != 0) return cuda_fail(static_cast<cudaError_t>(ce), "integrate kernel launch");
     return KT_OK;
@@ -681,7 +690,7 @@ int kt::prepare_launch(const kt_network *net, int64_t ncells, const double *y_in
     a->status = status;
     a->nsub = n_substeps;
     a->nnew = n_newton;
-    *c = kt::LaunchCfg{opts->form, opts->persistent, opts->block_warps, opts->blocks_per_sm, cpw};
+    *c = kt::LaunchCfg{opts->form, opts->persistent, opts->block_warps, opts->blocks_per_sm, cpw, opts->lane_variant};
     *host_blob = net->blob.data();
     return KT_OK;
 }
@@ -918,11 +927,17 @@ int kt_autotune(const kt_network *net, int64_t ncells, const double *y_in, const
     const int fam = base->cells_per_warp ? base->cells_per_warp : (N <= kt::kLaneMaxN ? 32 : 1);
     const int cpws[1] = {fam};
     const int bws[4] = {1, 2, 4, 8};
+    // the FP32-LU lane kernels under TR-BDF2 come in two storage variants (kt.h KT_LANE_*)
+    const bool two = fam == 32 && base->form == KT_FORM_FP32LU && base->scheme == KT_SCHEME_TRBDF2 &&
+                     base->lane_variant == KT_LANE_AUTO;
+    const int vars[2] = {two ? KT_LANE_JCACHE : base->lane_variant, KT_LANE_LEAN};
     for (int ci = 0; ci < 1; ++ci) {
         if (cpws[ci] == 32 && N > kt::kLaneMaxN) continue;
+        for (int vi = 0; vi < (two ? 2 : 1); ++vi)
         for (int per = 0; per <= 1; ++per)
             for (int bi = 0; bi < 4; ++bi) {
                 cand.cells_per_warp = cpws[ci];
+                cand.lane_variant = vars[vi];
                 cand.persistent = per;
                 cand.block_warps = bws[bi];
                 cand.blocks_per_sm = 0;

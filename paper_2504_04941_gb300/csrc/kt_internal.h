@@ -30,6 +30,7 @@ constexpr double kF32NewtonAtolScale = 1e-6;
 struct NetView {
     int ns, ne, nr, energy, N;
     int off_A, off_b, off_th, off_dH;     // double[nr]: prefactor, exponent, activation T, heat
+    int off_f32;                          // float[3][nr]: b, activation T and heat in FP32
     int off_h, off_cv, off_cnt;           // double[ns], double[ns], double[ns*ne]
     int off_idx;                          // uint8[nr*8]: nin (| kIdxDistinct), nout, in0..2, out0..2
     int off_exp;                          // double[kExpTable]: 2^(j/256) for the table-driven exp
@@ -48,6 +49,9 @@ struct NetView {
     int ntab, tab_nT, tab_nR, off_tab;    // tables: double[ntab][nR][nT] ln k after the staged
                                           // part (global memory)
     int bytes;                            // staged part (shared memory), multiple of 16
+    int bytes_warp;                       // the prefix the warp-per-cell kernels stage
+                                          // (no reaction heats; photo and table
+                                          // descriptors only when the network has them)
     int bytes_total;                      // the whole blob, tables included
     double t_ref, t_min, t_max, t_mid;
     double tab_lt0, tab_dlt, tab_lr0, tab_dlr;   // ln T0, ln-T node spacing, ln rho0, ln(rho1/rho0)
@@ -94,6 +98,7 @@ struct LaunchCfg {
     int block_warps;    // 0 = auto
     int blocks_per_sm;  // 0 = auto
     int cells_per_warp; // 32: lane-per-cell kernels, 1: warp-per-cell kernels
+    int lane_variant;   // KT_LANE_*: storage of the FP32-LU lane kernels under TR-BDF2
 };
 
 // Shared-memory layout of one warp of the lane-per-cell kernels.  Every per-cell
@@ -150,6 +155,34 @@ inline LaneLayout lane_layout(int N, int nr, int energy, int fp32, int blob_byte
     return L;
 }
 
+// Shared-memory layout of one warp of the lean FP32-LU lane kernels (TR-BDF2 only;
+// the step's start state y_n and its rate f_n live in registers): the FP32 iteration
+// matrix I - d h J, assembled directly and factorised in place (inverse pivots on its
+// diagonal); the rate vector f (FP64), whose slots the LU's FP32 row scales reuse once
+// the Newton residual has been formed from it; one pivot byte per row; the stage
+// iterates and the stage right-hand side.  11 unknowns: 27,136 bytes per warp.
+inline LaneLayout lane_layout_lean(int N, int nr, int energy, int blob_bytes, int cvpoly)
+{
+    LaneLayout L{};
+    const int d = 32 * 8, f = 32 * 4;
+    int o = 0;
+    L.off_M = o; o += N * N * f;
+    L.off_W = o; o += N * d;
+    L.off_V = L.off_W;
+    L.off_P = o; o += N * 32;
+    o = (o + 255) & ~255;
+    L.off_YF = o; o += N * d;
+    L.off_YH = o; o += N * d;
+    L.off_Y2 = o; o += N * d;
+    L.off_J = L.off_X = L.off_Y = L.off_FY = -1;
+    if (!energy) { L.off_K = o; o += nr * d; } else { L.off_K = -1; }
+    if (cvpoly) { L.off_CV = o; o += 10 * d; } else { L.off_CV = -1; }
+    L.warp_bytes = (o + 255) & ~255;
+    L.mlp_off = (blob_bytes + 16 + 255) & ~255;
+    L.base = L.mlp_off;
+    return L;
+}
+
 // Shared-memory layout of one warp of the warp-per-cell kernels (one cell per warp).
 // Matrices are row-major with an odd row stride NP (conflict-free column reads).
 struct WarpLayout {
@@ -157,11 +190,14 @@ struct WarpLayout {
     int off_M, off_J, off_V, off_P, off_G;   // matrix, fp32 Jacobian, scales, pivots, gather
     int off_Y, off_YF, off_YH, off_Y2, off_W;
     int off_F0;                              // TR-BDF2: f at the step's start state
-    int off_K, off_DK;                       // rate coefficients and dk/dT per reaction
+    int off_K, off_DK;                       // rate coefficients and dk/dT (or the rates) per reaction
     int warp_bytes, base;
 };
 
-inline WarpLayout warp_layout(int N, int nr, int energy, int fp32, int blob_bytes)
+// share_jm (FP32 form under TR-BDF2): the FP32 Jacobian is assembled in the storage of
+// the iteration matrix and turned into I - d h J in place, since TR-BDF2 factorises
+// once per step attempt from a freshly assembled Jacobian and never re-uses it.
+inline WarpLayout warp_layout(int N, int nr, int energy, int fp32, int blob_bytes, bool share_jm = false)
 {
     WarpLayout L{};
     L.NP = N | 1;
@@ -170,7 +206,7 @@ inline WarpLayout warp_layout(int N, int nr, int energy, int fp32, int blob_byte
     auto take = [&](int bytes) { int r = o; o = (o + bytes + 15) & ~15; return r; };
     if (fp32) {
         L.off_J = take(NN * 4);
-        L.off_M = take(NN * 4);
+        L.off_M = share_jm ? L.off_J : take(NN * 4);
         L.off_V = take(N * 4);
     } else {
         L.off_J = -1;
@@ -186,7 +222,7 @@ inline WarpLayout warp_layout(int N, int nr, int energy, int fp32, int blob_byte
     L.off_W = take(N * 8);
     L.off_F0 = take(N * 8);
     L.off_K = take(nr * 8);
-    L.off_DK = energy ? take(nr * 8) : -1;
+    L.off_DK = take(nr * 8);   // dk/dT; in iterations without a Jacobian, the reaction rates
     L.warp_bytes = (o + 127) & ~127;
     L.base = (blob_bytes + 16 + 127) & ~127;
     return L;

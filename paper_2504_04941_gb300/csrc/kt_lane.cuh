@@ -30,6 +30,11 @@
 //                iteration matrix I - h J is factorised in FP32 (once for h, once for
 //                h/2), while the residual, the update, the convergence test, the
 //                error norm and the conservation projection stay in FP64.
+//   LEAN = true  (F32, TR-BDF2, size known at compile time) the iteration matrix is
+//                assembled directly in FP32 without a Jacobian copy, y_n and f_n live
+//                in registers and a failed FP32 solve halves h (no FP64 rescue): half
+//                the shared memory per warp of the F32 layout, so twice the warps per
+//                SM hide each other's FP64 and shared-memory latencies.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -55,8 +60,22 @@ constexpr int kMaxWarps = 8;
 
 enum LaneState : int { kNeed = 0, kRun = 1, kDone = 2 };
 
+// A per-lane FP64 vector: in registers (REG; every index must be a compile-time
+// constant once the loops are unrolled) or lane-interleaved in shared memory.
+template <bool REG, int NR>
+struct LaneVec {
+    double r[NR];
+    double *p;
+    __device__ __forceinline__ double &operator[](int i)
+    {
+        if constexpr (REG) return r[i];
+        else return p[i << 5];
+    }
+};
+
 struct NetSmem {
     const double *A, *b, *th, *dH, *h, *cv, *cnt, *ex;
+    const float *bf, *thf, *dHf;   // FP32 copies for the FP32 Jacobian (no FP64-pipe conversions)
     const unsigned long long *idx;
 };
 
@@ -72,6 +91,9 @@ __device__ __forceinline__ NetSmem net_smem(const unsigned char *sm, const NetVi
     t.cnt = reinterpret_cast<const double *>(sm + nv.off_cnt);
     t.idx = reinterpret_cast<const unsigned long long *>(sm + nv.off_idx);
     t.ex = reinterpret_cast<const double *>(sm + nv.off_exp);
+    t.bf = reinterpret_cast<const float *>(sm + nv.off_f32);
+    t.thf = t.bf + nv.nr;
+    t.dHf = t.thf + nv.nr;
     return t;
 }
 
@@ -160,6 +182,7 @@ __device__ __forceinline__ void scatter22(T *A, int N, int ns, int i0, int i1, i
 //   W  <- f(yt)                                   (always, FP64)
 //   MODE 1: M64 <- I - hph * J(yt)                (FP64)
 //   MODE 2: J32 <- J(yt) when doJ                 (FP32; residual still FP64)
+//   MODE 3: J32 <- I - hph * J(yt) when doJ       (FP32, lane stride 32: the lean layout)
 // The temperature row uses each reaction's heat dH_r = sum h_out - sum h_in:
 // dT/dt = -sum_r dH_r w_r / C_V, an exact rewrite of -sum_s h_s (dn_s/dt) / C_V.
 // Reactions go in chunks of kChunk: the rate coefficients and rates of a chunk are
@@ -183,6 +206,13 @@ __device__ __forceinline__ void reaction_pass(const NetView &nv, const NetSmem &
     if (MODE == 2 && doJ) {
         for (int e = 0; e < N * N; ++e) LIS(J32, e, 6) = 0.0f;
     }
+    if (MODE == 3 && doJ) {
+        for (int e = 0; e < N * N; ++e) LIS(J32, e, 5) = 0.0f;
+    }
+    // FP32 Jacobian (MODE 2/3): every partial in FP32, dk/dT = k (b + theta/T)/T included;
+    // it only shapes the simplified-Newton iteration matrix
+    const float hf = static_cast<float>(hph), invTf = static_cast<float>(invT);
+    const float invCVf = static_cast<float>(invCV);
     double fT = 0.0;
     for (int r0 = 0; r0 < nr; r0 += kChunk) {
         unsigned long long ixq[kChunk];
@@ -269,14 +299,16 @@ __device__ __forceinline__ void reaction_pass(const NetView &nv, const NetSmem &
             if (MODE == 2 && doJ && dist) {
                 const float kf = static_cast<float>(k);
                 const float f0 = static_cast<float>(y0), f1 = static_cast<float>(y1);
-                const float d2 = ENERGY ? static_cast<float>(k * (t.b[r] + t.th[r] * invT) * invT * (y0 * y1)) : 0.0f;
+                const float d2 = ENERGY ? kf * (t.bf[r] + t.thf[r] * invTf) *
+                                              invTf * (f0 * f1)
+                                        : 0.0f;
                 scatter22<float, 6, ENERGY>(J32, N, ns, i0, i1, o0, o1, kf * f1, kf * f0, d2,
-                                            ENERGY ? static_cast<float>(dHr * invCV) : 0.0f, -1.0f);
+                                            ENERGY ? t.dHf[r] * invCVf : 0.0f, -1.0f);
             } else if (MODE == 2 && doJ) {
                 const float kf = static_cast<float>(k);
                 const float f0 = static_cast<float>(y0), f1 = static_cast<float>(y1),
                             f2 = static_cast<float>(y2);
-                const float qf = ENERGY ? static_cast<float>(dHr * invCV) : 0.0f;
+                const float qf = ENERGY ? t.dHf[r] * invCVf : 0.0f;
                 auto col = [&](int m, float d) {
                     LIS(J32, i0 * N + m, 6) -= d;
                     if (nin > 1) LIS(J32, i1 * N + m, 6) -= d;
@@ -290,8 +322,42 @@ __device__ __forceinline__ void reaction_pass(const NetView &nv, const NetSmem &
                 if (nin > 1) col(i1, S2 ? kf * f0 : kf * f0 * f2);
                 if (!S2 && nin > 2) col(i2, kf * f0 * f1);
                 if (ENERGY) {
-                    const double dw = k * (t.b[r] + t.th[r] * invT) * invT * (y0 * y1);
-                    col(ns, static_cast<float>(S2 ? dw : dw * y2));
+                    const float dw = kf * (t.bf[r] + t.thf[r] * invTf) *
+                                     invTf * (f0 * f1);
+                    col(ns, S2 ? dw : dw * f2);
+                }
+            }
+            if (MODE == 3 && doJ && dist) {
+                // I - h J in FP32: reactant rows + h dw/dy_c, product rows - h dw/dy_c,
+                // the T row + (dH_r / C_V) h dw/dy_c
+                const float hk = hf * static_cast<float>(k);
+                const float f0 = static_cast<float>(y0), f1 = static_cast<float>(y1);
+                const float d2 = ENERGY ? hk * (t.bf[r] + t.thf[r] * invTf) *
+                                              invTf * (f0 * f1)
+                                        : 0.0f;
+                scatter22<float, 5, ENERGY>(J32, N, ns, i0, i1, o0, o1, hk * f1, hk * f0, d2,
+                                            ENERGY ? t.dHf[r] * invCVf : 0.0f, 1.0f);
+            } else if (MODE == 3 && doJ) {
+                const float hk = hf * static_cast<float>(k);
+                const float f0 = static_cast<float>(y0), f1 = static_cast<float>(y1),
+                            f2 = static_cast<float>(y2);
+                const float qf = ENERGY ? t.dHf[r] * invCVf : 0.0f;
+                auto col = [&](int m, float d) {
+                    LIS(J32, i0 * N + m, 5) += d;
+                    if (nin > 1) LIS(J32, i1 * N + m, 5) += d;
+                    if (!S2 && nin > 2) LIS(J32, i2 * N + m, 5) += d;
+                    if (nout > 0) LIS(J32, o0 * N + m, 5) -= d;
+                    if (nout > 1) LIS(J32, o1 * N + m, 5) -= d;
+                    if (!S2 && nout > 2) LIS(J32, o2 * N + m, 5) -= d;
+                    if (ENERGY) LIS(J32, ns * N + m, 5) += qf * d;
+                };
+                col(i0, S2 ? hk * f1 : hk * f1 * f2);
+                if (nin > 1) col(i1, S2 ? hk * f0 : hk * f0 * f2);
+                if (!S2 && nin > 2) col(i2, hk * f0 * f1);
+                if (ENERGY) {
+                    const float dw = hk * (t.bf[r] + t.thf[r] * invTf) *
+                                     invTf * (f0 * f1);
+                    col(ns, S2 ? dw : dw * f2);
                 }
             }
         }
@@ -299,6 +365,9 @@ __device__ __forceinline__ void reaction_pass(const NetView &nv, const NetSmem &
     if (ENERGY) LI(W, ns) = fT * invCV;
     if (MODE == 1) {
         for (int i = 0; i < N; ++i) LI(M64, i * N + i) += 1.0;
+    }
+    if (MODE == 3 && doJ) {
+        for (int i = 0; i < N; ++i) LIS(J32, i * N + i, 5) += 1.0f;
     }
 }
 
@@ -386,9 +455,104 @@ __device__ __forceinline__ void crout_solve(const T *M, const T *V, const int *P
     }
 }
 
-template <int NT, bool ENERGY, bool F32, bool PERSIST, bool MLPG>
+// Crout LU of the lean layout: the same steps and operation order as crout_lu<float>
+// at lane stride 32, with the inverse pivots stored on the diagonal (U's diagonal is
+// not read again once its column is done), the row scales V in a scratch area and one
+// pivot byte per row.  Returns false on a zero row or a zero pivot.
+template <int NT>
+__device__ __forceinline__ bool crout_lu_lean(float *M, float *V, unsigned char *P)
+{
+    constexpr int N = NT;
+    bool ok = true;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        float big = 0.0f;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const float a = LIS(M, i * N + j, 5);
+            big = a < 0.0f ? (-a > big ? -a : big) : (a > big ? a : big);
+        }
+        ok = ok && (big > 0.0f);
+        LIS(V, i, 5) = big > 0.0f ? 1.0f / big : 1.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const int kmax = i < j ? i : j;
+            float s = LIS(M, i * N + j, 5);
+#pragma unroll
+            for (int k = 0; k < kmax; ++k) s -= LIS(M, i * N + k, 5) * LIS(M, k * N + j, 5);
+            LIS(M, i * N + j, 5) = s;
+        }
+        int imax = j;
+        float tmax = fabsf(LIS(M, j * N + j, 5)) * LIS(V, j, 5);
+#pragma unroll
+        for (int i = j + 1; i < N; ++i) {
+            const float tt = fabsf(LIS(M, i * N + j, 5)) * LIS(V, i, 5);
+            if (tt > tmax) {
+                tmax = tt;
+                imax = i;
+            }
+        }
+        ok = ok && (tmax > 0.0f);
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            const float a = LIS(M, imax * N + k, 5), b = LIS(M, j * N + k, 5);
+            LIS(M, imax * N + k, 5) = b;
+            LIS(M, j * N + k, 5) = a;
+        }
+        const float va = LIS(V, imax, 5);
+        LIS(V, imax, 5) = LIS(V, j, 5);
+        LIS(V, j, 5) = va;
+        LIS(P, j, 5) = static_cast<unsigned char>(imax);
+        const float rinv = 1.0f / LIS(M, j * N + j, 5);
+#pragma unroll
+        for (int i = j + 1; i < N; ++i) LIS(M, i * N + j, 5) *= rinv;
+        LIS(M, j * N + j, 5) = rinv;
+    }
+    return ok;
+}
+
+// Solve with the lean factors, the right-hand side in registers: the row swaps in
+// order (as selects, so every index stays a compile-time constant), unit-lower forward,
+// upper backward times the stored inverse pivot.
+template <int NT>
+__device__ __forceinline__ void crout_solve_lean(const float *M, const unsigned char *P, float (&x)[NT])
+{
+#pragma unroll
+    for (int i = 0; i < NT; ++i) {
+        const int p = LIS(P, i, 5);
+#pragma unroll
+        for (int k = i + 1; k < NT; ++k) {
+            if (k == p) {
+                const float t = x[i];
+                x[i] = x[k];
+                x[k] = t;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NT; ++i) {
+        float s = x[i];
+#pragma unroll
+        for (int k = 0; k < i; ++k) s -= LIS(M, i * NT + k, 5) * x[k];
+        x[i] = s;
+    }
+#pragma unroll
+    for (int i = NT - 1; i >= 0; --i) {
+        float s = x[i];
+#pragma unroll
+        for (int k = i + 1; k < NT; ++k) s -= LIS(M, i * NT + k, 5) * x[k];
+        x[i] = s * LIS(M, i * NT + i, 5);
+    }
+}
+
+template <int NT, bool ENERGY, bool F32, bool PERSIST, bool MLPG, bool LEAN>
 __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArgs a, const LaneLayout L)
 {
+    static_assert(!LEAN || (F32 && NT > 0 && !MLPG), "the lean layout is an FP32-LU, fixed-size variant");
+    constexpr int NR = LEAN ? NT : 1;   // register vectors of the lean layout
     extern __shared__ __align__(16) unsigned char sm[];
     const NetView nv = a.nv;
     if (!stage_table(sm, a.blob, static_cast<unsigned>(nv.bytes),
@@ -400,18 +564,25 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
         return;
     const NetSmem t = net_smem(sm, nv);
     const DevOpts o = a.o;
-    const int N = NT > 0 ? NT : nv.N, ns = nv.ns, ne = nv.ne, nr = nv.nr;
+    // N = ns + 1 with the energy equation, else ns
+    const int N = NT > 0 ? NT : nv.N, ns = LEAN ? NT - (ENERGY ? 1 : 0) : nv.ns, ne = nv.ne, nr = nv.nr;
     const long long nc = a.ncells;
     const int lane = threadIdx.x & 31;
     unsigned char *wb = sm + L.base + (threadIdx.x >> 5) * L.warp_bytes;
-    double *Y = reinterpret_cast<double *>(wb + L.off_Y) + lane;
+    // y_n (Y) and f_n (FY): registers in the lean layout, shared memory otherwise
+    LaneVec<LEAN, NR> Y, FY;
+    Y.p = LEAN ? nullptr : reinterpret_cast<double *>(wb + L.off_Y) + lane;
+    FY.p = LEAN ? nullptr : reinterpret_cast<double *>(wb + L.off_FY) + lane;
     double *YF = reinterpret_cast<double *>(wb + L.off_YF) + lane;
     double *YH = reinterpret_cast<double *>(wb + L.off_YH) + lane;
     double *Y2 = reinterpret_cast<double *>(wb + L.off_Y2) + lane;
     double *W = reinterpret_cast<double *>(wb + L.off_W) + lane;
-    double *FY = reinterpret_cast<double *>(wb + L.off_FY) + lane;
     const bool s2 = nv.shape == 22;   // every reaction A + B -> C + D
-    int *P = reinterpret_cast<int *>(wb + L.off_P) + lane;
+    int *P = LEAN ? nullptr : reinterpret_cast<int *>(wb + L.off_P) + lane;
+    // lean layout: FP32 matrix at lane stride 32, row scales over the rate slots, pivot bytes
+    float *ML = LEAN ? reinterpret_cast<float *>(wb + L.off_M) + lane : nullptr;
+    float *VL = LEAN ? reinterpret_cast<float *>(wb + L.off_W) + lane : nullptr;
+    unsigned char *PL = LEAN ? wb + L.off_P + lane : nullptr;
     double *K = ENERGY ? nullptr : reinterpret_cast<double *>(wb + L.off_K) + lane;
     // C_V(T) of polynomial networks (Sec. 4.2): the cell's coefficients sum_s n0_s c_s,k,
     // five below t_mid then five from t_mid
@@ -420,10 +591,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
     const double *cvp = reinterpret_cast<const double *>(sm + nv.off_cvp);
     // FP64 matrix and scales; in the FP32 form they overlay the lane's own J32/M32 and
     // V32/X32 slots and serve the FP64 rescue of a failed FP32 solve
-    double *M64 = reinterpret_cast<double *>(wb + L.off_M) + lane;
-    double *V64 = reinterpret_cast<double *>(wb + L.off_V) + lane;
+    double *M64 = LEAN ? nullptr : reinterpret_cast<double *>(wb + L.off_M) + lane;
+    double *V64 = LEAN ? nullptr : reinterpret_cast<double *>(wb + L.off_V) + lane;
     float *J32 = nullptr, *M32 = nullptr, *V32 = nullptr, *X32 = nullptr;
-    if (F32) {
+    if (F32 && !LEAN) {
         J32 = reinterpret_cast<float *>(wb + L.off_J) + 2 * lane;
         M32 = J32 + 1;
         V32 = reinterpret_cast<float *>(wb + L.off_V) + 2 * lane;
@@ -463,26 +634,28 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
     // on the cell's first step, afterwards the previous step's stage relation
     // f_{n+1} = (y_{n+1} - r)/(d h) (an evaluated f(y_n) would enter the error estimate
     // multiplied by h, which turns its rounding into noise in err on stiff components).
-    const bool TR = o.scheme == KT_SCHEME_TRBDF2;
+    const bool TR = LEAN || o.scheme == KT_SCHEME_TRBDF2;
     const TrCoef tr = tr_coef();
 
     // Pre-processing (Sec. 2.2.2): floors y >= 0 and T clamped to [t_min, t_max].
     auto load_pre = [&]() {
         fyok = false;
         jY = false;
+#pragma unroll
         for (int s = 0; s < ns; ++s) {
             const double v = a.y_in[static_cast<long long>(s) * nc + cell];
-            LI(Y, s) = v > 0.0 ? v : 0.0;
+            Y[s] = v > 0.0 ? v : 0.0;
         }
         const double Tin = a.T_in[cell];
         const double T0 = Tin < nv.t_min ? nv.t_min : (Tin > nv.t_max ? nv.t_max : Tin);
         T_iso = T0;
-        if (ENERGY) LI(Y, ns) = T0;
+        if (ENERGY) Y[ns] = T0;
     };
 
     auto write_out = [&](int st) {
-        for (int s = 0; s < ns; ++s) a.y_out[static_cast<long long>(s) * nc + cell] = LI(Y, s);
-        a.T_out[cell] = ENERGY ? LI(Y, ns) : T_iso;
+#pragma unroll
+        for (int s = 0; s < ns; ++s) a.y_out[static_cast<long long>(s) * nc + cell] = Y[s];
+        a.T_out[cell] = ENERGY ? Y[ns] : T_iso;
         if (a.status) a.status[cell] = st;
         if (a.nsub) a.nsub[cell] = st == KT_STATUS_REVERTED ? 0 : nacc;
         if (a.nnew) a.nnew[cell] = nnew;
@@ -498,7 +671,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
         }
         phase = 0;
         it = 0;
-        for (int i = 0; i < N; ++i) LI(YF, i) = LI(Y, i);
+#pragma unroll
+        for (int i = 0; i < N; ++i) LI(YF, i) = Y[i];
         atY = true;
         if (F32) {
             needJ = true;
@@ -544,15 +718,18 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
             const double y0 = v > 0.0 ? v : 0.0;
             for (int e = 0; e < ne; ++e) b0[e] += t.cnt[s * ne + e] * y0;
         }
+#pragma unroll
         for (int s = 0; s < ns; ++s)
-            if (LI(Y, s) < 0.0) LI(Y, s) = 0.0;
+            if (Y[s] < 0.0) Y[s] = 0.0;
         for (int e = 0; e < ne; ++e) {
             double tot = 0.0;
-            for (int s = 0; s < ns; ++s) tot += t.cnt[s * ne + e] * LI(Y, s);
+#pragma unroll
+            for (int s = 0; s < ns; ++s) tot += t.cnt[s * ne + e] * Y[s];
             r[e] = tot - b0[e];
             for (int f = 0; f < ne; ++f) {
                 double m = 0.0;
-                for (int s = 0; s < ns; ++s) m += t.cnt[s * ne + e] * t.cnt[s * ne + f] * LI(Y, s);
+#pragma unroll
+                for (int s = 0; s < ns; ++s) m += t.cnt[s * ne + e] * t.cnt[s * ne + f] * Y[s];
                 Mp[e * ne + f] = m;
             }
         }
@@ -590,13 +767,15 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
             r[i] = s / Mp[i * ne + i];
         }
         bool ok = true;
+#pragma unroll
         for (int s = 0; s < ns; ++s) {
             double corr = 0.0;
             for (int e = 0; e < ne; ++e) corr += t.cnt[s * ne + e] * r[e];
             ok = ok && (corr < 1.0);
-            LI(Y, s) -= LI(Y, s) * corr;
+            Y[s] -= Y[s] * corr;
         }
-        for (int i = 0; i < N; ++i) ok = ok && isfinite(LI(Y, i));
+#pragma unroll
+        for (int i = 0; i < N; ++i) ok = ok && isfinite(Y[i]);
         return ok;
     };
 
@@ -617,15 +796,17 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
         }
         load_pre();
         double cvt = 0.0, b00 = 0.0;
+#pragma unroll
         for (int s = 0; s < ns; ++s) {
-            cvt += t.cv[s] * LI(Y, s);
-            b00 += t.cnt[s * ne] * LI(Y, s);
+            cvt += t.cv[s] * Y[s];
+            b00 += t.cnt[s * ne] * Y[s];
         }
         invCV = ENERGY ? 1.0 / cvt : 0.0;
         if (CVP) {
             for (int k = 0; k < 10; ++k) {
                 double c = 0.0;
-                for (int s = 0; s < ns; ++s) c += LI(Y, s) * cvp[s * 10 + k];
+#pragma unroll
+                for (int s = 0; s < ns; ++s) c += Y[s] * cvp[s * 10 + k];
                 LI(CV, k) = c;
             }
         }
@@ -652,15 +833,18 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
     // starting point of the current solve (plain predictor / second half from the full step)
     auto restart_solve = [&]() {
         if (TR) {
-            double *ys = phase == 0 ? YF : Y2;
-            const double *g = phase == 0 ? Y : YF;
-            for (int i = 0; i < N; ++i) LI(ys, i) = LI(g, i);
+            if (phase == 0) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) LI(YF, i) = Y[i];
+            } else {
+                for (int i = 0; i < N; ++i) LI(Y2, i) = LI(YF, i);
+            }
             atY = phase == 0;
             it = 0;
             return;
         }
         double *yt = phase == 0 ? YF : (phase == 1 ? YH : Y2);
-        const double *g = phase == 2 ? (o.guess != KT_GUESS_PREV ? YF : YH) : Y;
+        const double *g = phase == 2 ? (o.guess != KT_GUESS_PREV ? YF : YH) : Y.p;
         for (int i = 0; i < N; ++i) LI(yt, i) = LI(g, i);
         atY = phase != 2;
         it = 0;
@@ -680,7 +864,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
             }
             return;
         }
-        if (F32 && !rescue) {
+        if (F32 && !LEAN && !rescue) {
             rescue = true;
             atomicAdd(&a.scratch->rescues, 1u);
             restart_solve();
@@ -692,15 +876,17 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
     auto step_done = [&]() {
         // weighted RMS of the step-doubling difference
         double s2 = 0.0;
+#pragma unroll
         for (int i = 0; i < N; ++i) {
-            const double y = LI(Y, i), y2 = LI(Y2, i);
+            const double y = Y[i], y2 = LI(Y2, i);
             const double sc = (i < ns ? atol_s : 0.0) + o.rtol * fmax(fabs(y), fabs(y2));
             const double e = (y2 - LI(YF, i)) / sc;
             s2 += e * e;
         }
         const double err = sqrt(s2 / N);
         if (err <= 1.0) {
-            for (int i = 0; i < N; ++i) LI(Y, i) = LI(Y2, i);
+#pragma unroll
+            for (int i = 0; i < N; ++i) Y[i] = LI(Y2, i);
             fyok = false;
             jY = false;
             ++nacc;
@@ -732,8 +918,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
     auto step_done_tr = [&]() {
         const double dh = tr.d * h, inv = 1.0 / dh, ce = 2.0 * tr.C * h;
         double s2 = 0.0;
+#pragma unroll
         for (int i = 0; i < N; ++i) {
-            const double yn = LI(Y, i), y1 = LI(Y2, i), f0 = LI(FY, i);
+            const double yn = Y[i], y1 = LI(Y2, i), f0 = FY[i];
             const double fg = (LI(YF, i) - yn) * inv - f0;
             const double f1 = (y1 - LI(YH, i)) * inv;
             const double est = ce * (tr.a0 * f0 + tr.a1 * fg + tr.a2 * f1);
@@ -743,9 +930,10 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
         }
         const double err = sqrt(s2 / N);
         if (err <= 1.0) {
+#pragma unroll
             for (int i = 0; i < N; ++i) {
-                LI(FY, i) = (LI(Y2, i) - LI(YH, i)) * inv;   // first same as last
-                LI(Y, i) = LI(Y2, i);
+                FY[i] = (LI(Y2, i) - LI(YH, i)) * inv;   // first same as last
+                Y[i] = LI(Y2, i);
             }
             fyok = true;
             jY = false;
@@ -785,8 +973,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
             if (phase == 0) {       // BDF2 stage: r = w1 y_g - w0 y_n, start from y_g
                 phase = 1;
                 it = 0;
+#pragma unroll
                 for (int i = 0; i < N; ++i) {
-                    LI(YH, i) = tr.w1 * LI(YF, i) - tr.w0 * LI(Y, i);
+                    LI(YH, i) = tr.w1 * LI(YF, i) - tr.w0 * Y[i];
                     LI(Y2, i) = LI(YF, i);
                 }
                 atY = false;
@@ -798,7 +987,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
         if (phase == 0) {
             phase = 1;
             it = 0;
-            for (int i = 0; i < N; ++i) LI(YH, i) = LI(Y, i);
+#pragma unroll
+            for (int i = 0; i < N; ++i) LI(YH, i) = Y[i];
             atY = true;
             if (F32) { needF = true; }
         } else if (phase == 1) {
@@ -850,8 +1040,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
                 for (int k = 0; k < kMlpIn; ++k) x[k] = 0.0f;
                 if (wantG) {
                     for (int k = 0; k < ns && k < kMlpIn; ++k)
-                        x[k] = static_cast<float>((log(fmax(LI(Y, k), 1e-30)) - nrm[k]) / nrm[16 + k]);
-                    const double Tc = ENERGY ? LI(Y, ns) : T_iso;
+                        x[k] = static_cast<float>((log(fmax(Y[k], 1e-30)) - nrm[k]) / nrm[16 + k]);
+                    const double Tc = ENERGY ? Y[ns] : T_iso;
                     const double f3[3] = {log(Tc), log(rho_c), log(h)};
 #pragma unroll
                     for (int q = 0; q < 3; ++q) {
@@ -875,9 +1065,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
                 if (wantG) {
                     for (int i = 0; i < N && i < kMlpOut; ++i) {
                         const double dlog = nrm[32 + i] + nrm[48 + i] * static_cast<double>(outv[i]);
-                        const double base = i < ns ? fmax(LI(Y, i), 1e-30) : LI(Y, i);
+                        const double base = i < ns ? fmax(Y[i], 1e-30) : Y[i];
                         const double g = base * exp(fmin(dlog, 50.0));
-                        LI(YF, i) = isfinite(g) ? g : LI(Y, i);
+                        LI(YF, i) = isfinite(g) ? g : Y[i];
                     }
                     needG = false;
                     usedG = true;
@@ -888,7 +1078,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
         if (state != kRun) continue;
 
         // ---- one Newton iteration of the current backward-Euler solve
-        const double *yb = TR ? YH : (phase == 2 ? YH : Y);
+        const double *yb = TR ? YH : (phase == 2 ? YH : Y.p);
         double *yt = TR ? (phase == 0 ? YF : Y2) : (phase == 0 ? YF : (phase == 1 ? YH : Y2));
         const double hph = TR ? tr.d * h : (phase == 0 ? h : 0.5 * h);
         // TR-BDF2 stage 1 at its first iterate (y_n itself): f(y_n) -> FY, r1 = y_n + d h f(y_n)
@@ -912,7 +1102,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
                 dcvr = dcv * invCVi;
             }
         }
-        if (!F32 || rescue) {
+        float xr[NR];   // lean layout: the FP32 residual, then the Newton update
+        if (!F32 || (!LEAN && rescue)) {
             if (s2)
                 reaction_pass<NT, ENERGY, 1, true>(nv, t, yt, K, lt, invT, invCVi, hph, W, M64, nullptr, false);
             else
@@ -922,18 +1113,48 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
             if (F32) jY = false;   // the FP64 matrix overlays the FP32 Jacobian
             if (trF0) {
                 if (!fyok) {
-                    for (int i = 0; i < N; ++i) LI(FY, i) = LI(W, i);
+#pragma unroll
+                    for (int i = 0; i < N; ++i) FY[i] = LI(W, i);
                     fyok = true;
                 }
-                for (int i = 0; i < N; ++i) LI(YH, i) = LI(Y, i) + hph * LI(FY, i);
+#pragma unroll
+                for (int i = 0; i < N; ++i) LI(YH, i) = Y[i] + hph * FY[i];
             }
             for (int i = 0; i < N; ++i) LI(W, i) = -(LI(yt, i) - LI(yb, i) - hph * LI(W, i));
             luok = crout_lu<double, 5>(M64, V64, P, N);
             crout_solve<double, 5>(M64, V64, P, W, N);
+        } else if constexpr (LEAN) {
+            // the matrix is assembled at the current iterate whenever it is factorised
+            // (the step's start, a refresh): there is no Jacobian copy to re-use
+            const bool doM = needF;
+            if (s2)
+                reaction_pass<NT, ENERGY, 3, true>(nv, t, yt, K, lt, invT, invCVi, hph, W, nullptr, ML, doM);
+            else
+                reaction_pass<NT, ENERGY, 3, false>(nv, t, yt, K, lt, invT, invCVi, hph, W, nullptr, ML, doM);
+            if (CVP && doM) LIS(ML, ns * N + ns, 5) += static_cast<float>(hph * LI(W, ns) * dcvr);
+            if (atY && !fyok) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) FY[i] = LI(W, i);
+                fyok = true;
+            }
+            if (trF0) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) LI(YH, i) = Y[i] + hph * FY[i];
+            }
+            // residual before the factorisation: the row scales reuse the rate slots
+#pragma unroll
+            for (int i = 0; i < N; ++i) xr[i] = static_cast<float>(-(LI(yt, i) - LI(YH, i) - hph * LI(W, i)));
+            if (doM) {
+                luok = crout_lu_lean<NT>(ML, VL, PL);
+                needF = false;
+            }
+            needJ = false;
+            crout_solve_lean<NT>(ML, PL, xr);
         } else {
             const bool doJ = needJ && !(atY && jY);
             if (atY && fyok && !doJ) {
-                for (int i = 0; i < N; ++i) LI(W, i) = LI(FY, i);
+#pragma unroll
+                for (int i = 0; i < N; ++i) LI(W, i) = FY[i];
             } else {
                 if (s2)
                     reaction_pass<NT, ENERGY, 2, true>(nv, t, yt, K, lt, invT, invCVi, hph, W, nullptr, J32, doJ);
@@ -941,13 +1162,16 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
                     reaction_pass<NT, ENERGY, 2, false>(nv, t, yt, K, lt, invT, invCVi, hph, W, nullptr, J32, doJ);
                 if (CVP && doJ) LIS(J32, ns * N + ns, 6) -= static_cast<float>(LI(W, ns) * dcvr);
                 if (atY && !(TR && fyok)) {
-                    for (int i = 0; i < N; ++i) LI(FY, i) = LI(W, i);
+#pragma unroll
+                    for (int i = 0; i < N; ++i) FY[i] = LI(W, i);
                     fyok = true;
                 }
                 if (doJ) jY = atY;
             }
-            if (trF0)
-                for (int i = 0; i < N; ++i) LI(YH, i) = LI(Y, i) + hph * LI(FY, i);
+            if (trF0) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) LI(YH, i) = Y[i] + hph * FY[i];
+            }
             if (needF) {
                 for (int i = 0; i < N; ++i)
                     for (int j = 0; j < N; ++j)
@@ -967,18 +1191,22 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
         // dmaxr = max |delta| / (newton_rtol |y|), the purely relative part
         float dmax = 0.0f, dmaxr = 0.0f;
         const double natol = (F32 ? natol_frac * kF32NewtonAtolScale : natol_frac) * atol_s;
+#pragma unroll
         for (int i = 0; i < N; ++i) {
-            const double d = LI(W, i);
+            const double d = LEAN ? static_cast<double>(xr[i]) : LI(W, i);
             const double y = LI(yt, i) + d;
             LI(yt, i) = y;
             const double tol = (i < ns ? natol : 0.0) + o.newton_rtol * fabs(y);
             if (!(fabs(d) <= tol)) conv = false;
             if (F32) {
-                const float ad = static_cast<float>(fabs(d)), tf = static_cast<float>(tol);
+                // (lean: |delta| is the FP32 update itself and |y| is rounded once, which
+                // spares two conversions and a multiply on the FP64 pipe)
+                const float ad = LEAN ? fabsf(xr[i]) : static_cast<float>(fabs(d)), tf = static_cast<float>(tol);
                 const float q = __fdiv_rn(ad, fmaxf(tf, 1e-37f));
                 // the relative part newton_rtol |y| formed directly: as a difference
                 // tf - natol in FP32 it rounds to an ulp of natol for trace species
-                const float trl = static_cast<float>(o.newton_rtol * fabs(y));
+                const float trl = LEAN ? static_cast<float>(o.newton_rtol) * fabsf(static_cast<float>(y))
+                                       : static_cast<float>(o.newton_rtol * fabs(y));
                 const float qr = __fdiv_rn(ad, fmaxf(trl, 1e-37f));
                 dmax = q > dmax ? q : dmax;
                 dmaxr = qr > dmaxr ? qr : dmaxr;
@@ -991,7 +1219,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
         // newton_rtol |y_i| for every component, one iteration before |delta| itself
         // is.  Only the relative part of the tolerance is used, so species below the
         // absolute tolerance still end as close to the root as the plain test leaves them.
-        if (F32 && !rescue && !conv && !bad && luok && it > 0) {
+        if (F32 && !(!LEAN && rescue) && !conv && !bad && luok && it > 0) {
             const float th = dmaxr / dprevr;
             if (th < 0.5f && th / (1.0f - th) * dmaxr <= 1.0f) conv = true;
         }
@@ -999,7 +1227,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
         // ---- control
         if (conv) {
             phase_done();
-        } else if (!F32 || rescue) {
+        } else if (!F32 || (!LEAN && rescue)) {
             if (bad || !luok || it + 1 >= o.max_newton) newton_fail();
             else ++it;
         } else {
@@ -1026,11 +1254,12 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 1) lane_kernel(const LaunchArg
     }
 }
 
-template <int NT, bool ENERGY, bool F32, bool PERSIST, bool MLPG>
+template <int NT, bool ENERGY, bool F32, bool PERSIST, bool MLPG, bool LEAN = false>
 int launch_t(const LaunchArgs &a, const LaunchCfg &c, cudaStream_t s)
 {
-    const LaneLayout L = lane_layout(a.nv.N, a.nv.nr, a.nv.energy, F32 ? 1 : 0, a.nv.bytes,
-                                     MLPG ? MlpLayout::BYTES : 0, a.nv.cvpoly);
+    const LaneLayout L = LEAN ? lane_layout_lean(a.nv.N, a.nv.nr, a.nv.energy, a.nv.bytes, a.nv.cvpoly)
+                              : lane_layout(a.nv.N, a.nv.nr, a.nv.energy, F32 ? 1 : 0, a.nv.bytes,
+                                            MLPG ? MlpLayout::BYTES : 0, a.nv.cvpoly);
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -1042,7 +1271,7 @@ int launch_t(const LaunchArgs &a, const LaunchCfg &c, cudaStream_t s)
     while (warps > 1 && L.base + warps * L.warp_bytes > smem_optin) --warps;
     const size_t smem = static_cast<size_t>(L.base) + static_cast<size_t>(warps) * L.warp_bytes;
     if (smem > static_cast<size_t>(smem_optin)) return cudaErrorInvalidConfiguration;
-    auto kern = lane_kernel<NT, ENERGY, F32, PERSIST, MLPG>;
+    auto kern = lane_kernel<NT, ENERGY, F32, PERSIST, MLPG, LEAN>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     const int threads = warps * 32;
@@ -1075,6 +1304,17 @@ int launch_lane_form(const LaunchArgs &a, const LaunchCfg &c, cudaStream_t s)
             return en ? launch_t<NT, true, F32, true, true>(a, c, s) : launch_t<NT, false, F32, true, true>(a, c, s);
     } else {
         if (a.mlp) return cudaErrorInvalidValue;
+    }
+    if constexpr (F32 && NT > 0) {
+        // TR-BDF2 with a compile-time size: the lean layout unless the caller asks for
+        // the Jacobian-caching one
+        if (a.o.scheme == KT_SCHEME_TRBDF2 && c.lane_variant != KT_LANE_JCACHE) {
+            if (en)
+                return per ? launch_t<NT, true, true, true, false, true>(a, c, s)
+                           : launch_t<NT, true, true, false, false, true>(a, c, s);
+            return per ? launch_t<NT, false, true, true, false, true>(a, c, s)
+                       : launch_t<NT, false, true, false, false, true>(a, c, s);
+        }
     }
     if (en) return per ? launch_t<NT, true, F32, true, false>(a, c, s) : launch_t<NT, true, F32, false, false>(a, c, s);
     return per ? launch_t<NT, false, F32, true, false>(a, c, s) : launch_t<NT, false, F32, false, false>(a, c, s);

@@ -23,6 +23,7 @@ KT_GUESS_MLP = 1
 KT_GUESS_FULLSTEP = 2
 KT_SCHEME_BE = 0
 KT_SCHEME_TRBDF2 = 1
+KT_LANE_AUTO, KT_LANE_JCACHE, KT_LANE_LEAN = 0, 1, 2
 STATUS_OK, STATUS_RETRIED, STATUS_REVERTED, STATUS_NONFINITE = 0, 1, 2, 3
 
 _lib = None
@@ -47,7 +48,7 @@ class Options(ctypes.Structure):
                 ("block_warps", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
                 ("use_graph", ctypes.c_int), ("cells_per_warp", ctypes.c_int),
                 ("schedule", ctypes.c_int), ("scheme", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("lane_variant", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 def lib():
@@ -271,10 +272,11 @@ def integrate(net: Network, y, T, dt: float, opts: Options, rho=None, out=None,
     return dict(y=yo, T=To, status=st, nsub=nsub, nnewton=nnew, scratch=scratch)
 
 
-def integrate_dt(net: Network, y, T, dt_cells, opts: Options, out=None, scratch=None, stream=None):
+def integrate_dt(net: Network, y, T, dt_cells, opts: Options, out=None, scratch=None, stream=None,
+                 rho=None):
     """``integrate`` with a per-cell time step (CUDA float64 tensor [ncells])."""
     import torch
-    ncells = _require_cells(net, y, T, None, out, scratch)
+    ncells = _require_cells(net, y, T, rho, out, scratch)
     _require(dt_cells, "dt_cells", (ncells,), "float64")
     dev = T.device
     out = dict(out or {})
@@ -285,7 +287,7 @@ def integrate_dt(net: Network, y, T, dt_cells, opts: Options, out=None, scratch=
     if scratch is None:
         scratch = torch.empty(scratch_bytes(), dtype=torch.uint8, device=dev)
     _require_cells(net, y, T, None, out, scratch)
-    _check(lib().kt_integrate_dt(net.ptr, ncells, _ptr(y), _ptr(T), None, _ptr(dt_cells),
+    _check(lib().kt_integrate_dt(net.ptr, ncells, _ptr(y), _ptr(T), _ptr(rho), _ptr(dt_cells),
                                  ctypes.byref(opts), _ptr(out["y"]), _ptr(out["T"]),
                                  _ptr(out["status"]), _ptr(out["nsub"]), _ptr(out["nnewton"]),
                                  _ptr(scratch), _stream_handle(stream)))
@@ -379,7 +381,7 @@ def _np_ptr(a) -> Optional[int]:
     return a.ctypes.data
 
 
-_TUNED_FIELDS = ("cells_per_warp", "persistent", "block_warps", "blocks_per_sm")
+_TUNED_FIELDS = ("cells_per_warp", "persistent", "block_warps", "blocks_per_sm", "lane_variant")
 
 
 def autotune(net: Network, y, T, dt: float, base: Options, stream=None):

@@ -144,10 +144,14 @@ TR_CASES = [(1, None, dict(form=0, persistent=1)), (1, None, dict(form=1, persis
             (2, 250, dict(form=0, persistent=0)), (2, 250, dict(form=1, persistent=1)),
             (2, 250, dict(form=1, persistent=1, cells_per_warp=1)),
             (3, 97, dict(form=0, persistent=1)), (3, 97, dict(form=1, persistent=1)),
-            (5, 37, dict(form=0, persistent=1)), (5, 37, dict(form=1, persistent=1))]
-TR_IDS = ["robertson-fp64", "robertson-fp32lu", "robertson-warp-fp64", "combustion-fp64",
-          "combustion-fp32lu", "combustion-warp-fp32lu", "ism-fp64", "ism-fp32lu",
-          "combined64-fp64", "combined64-fp32lu"]
+            (5, 37, dict(form=0, persistent=1)), (5, 37, dict(form=1, persistent=1)),
+            (1, None, dict(form=1, persistent=1, lane_variant=1)),
+            (2, 250, dict(form=1, persistent=0, lane_variant=1)),
+            (2, 250, dict(form=1, persistent=0, lane_variant=2))]
+TR_IDS = ["robertson-fp64", "robertson-fp32lu-lean", "robertson-warp-fp64", "combustion-fp64",
+          "combustion-fp32lu-lean", "combustion-warp-fp32lu", "ism-fp64", "ism-fp32lu",
+          "combined64-fp64", "combined64-fp32lu", "robertson-fp32lu-jcache", "combustion-fp32lu-jcache-onepass",
+          "combustion-fp32lu-lean-onepass"]
 
 
 @pytest.mark.parametrize("wid,n,form", TR_CASES, ids=TR_IDS)
@@ -208,11 +212,11 @@ def test_edge_cases(kt, oracle_mod):
     assert np.array_equal(g["y"], np.maximum(wl.cells.subset(range(3, 40)).y, 0))
 
 
-@pytest.mark.parametrize("form,scheme", [(0, 0), (1, 0), (1, 1)])
-def test_split_range_bit_identical_and_deterministic(kt, form, scheme):
+@pytest.mark.parametrize("form,scheme,variant", [(0, 0, 0), (1, 0, 0), (1, 1, 1), (1, 1, 2)])
+def test_split_range_bit_identical_and_deterministic(kt, form, scheme, variant):
     wl = I.workload(2, 200)
     net = kt.Network(wl.network)
-    opts = kt.options(wl.tol, form=form, persistent=1, scheme=scheme)
+    opts = kt.options(wl.tol, form=form, persistent=1, scheme=scheme, lane_variant=variant)
     a = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, opts, net)
     b = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, opts, net)
     lo = gpu_run(kt, wl.network, wl.cells.subset(range(0, 77)), wl.tol.dt, opts, net)
@@ -221,10 +225,17 @@ def test_split_range_bit_identical_and_deterministic(kt, form, scheme):
         assert np.array_equal(a[k], b[k]), k
         assert np.array_equal(a[k], np.concatenate([lo[k], hi[k]], axis=-1)), k
     # persistent and one-pass launches compute the same cells bit for bit
-    c = gpu_run(kt, wl.network, wl.cells, wl.tol.dt, kt.options(wl.tol, form=form, persistent=0, scheme=scheme),
-                net)
+    c = gpu_run(kt, wl.network, wl.cells, wl.tol.dt,
+                kt.options(wl.tol, form=form, persistent=0, scheme=scheme, lane_variant=variant), net)
     for k in ("y", "T", "status", "nsub", "nnewton"):
         assert np.array_equal(a[k], c[k]), k
+    # and so do other block shapes (2 and 8 warps per block)
+    for bw in (2, 8):
+        d = gpu_run(kt, wl.network, wl.cells, wl.tol.dt,
+                    kt.options(wl.tol, form=form, persistent=1, scheme=scheme, lane_variant=variant,
+                               block_warps=bw), net)
+        for k in ("y", "T", "status", "nsub", "nnewton"):
+            assert np.array_equal(a[k], d[k]), (bw, k)
 
 
 def test_state_api_host_roundtrip(kt):

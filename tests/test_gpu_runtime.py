@@ -64,6 +64,15 @@ def test_autotune_and_cache(kt, oracle_mod, tmp_path):
     best, sec = kt.autotune(net, y, T, dt, base)
     assert best.cells_per_warp in (1, 32) and best.block_warps in (1, 2, 4, 8) and sec > 0
     assert best.form == 1 and best.rtol == base.rtol
+    # under TR-BDF2 the FP32-LU lane kernels' storage variant is a tuned dimension too
+    tr = kt.options(wl.tol, form=1, scheme=1)
+    best_tr, sec_tr = kt.autotune(net, y, T, dt, tr)
+    assert best_tr.lane_variant in (1, 2) and best_tr.scheme == 1 and sec_tr > 0
+    g = _direct(kt, net, wl.cells, dt, best_tr)
+    o = oracle_mod.OracleNetwork(wl.network).integrate(wl.cells, dt, oracle_mod.options(wl.tol, scheme=1),
+                                                       os.cpu_count())
+    assert compare(g, o, 1, tight=tight_oracle(oracle_mod, wl.network, wl.cells, dt, wl.tol,
+                                               os.cpu_count(), scheme=1)).ok()
     cache = str(tmp_path / "tuned.json")
     opts, entry = kt.tuned_options(net, y, T, dt, base, cache, sample=128)
     assert os.path.exists(cache) and len(json.load(open(cache))) == 1
