@@ -58,6 +58,28 @@ def test_options_default_and_network_parse(kt, tmp_path):
     assert ei.value.code == -4
 
 
+def test_options_lane_variant_default_and_range(kt):
+    """lane_variant defaults to automatic and an out-of-range value is refused by the
+    option check before any device work (a NULL-buffer call on zero cells)."""
+    import ctypes as C
+    from paper_2504_04941_gb300 import inputs as I
+    o = kt.options()
+    # 9 doubles and 16 ints: lane_variant took one of the reserved ints, the size is unchanged
+    assert o.lane_variant == kt.KT_LANE_AUTO and C.sizeof(kt.Options) == 9 * 8 + 16 * 4
+    net = kt.Network(I.network(2))
+    L = kt.lib()
+    for bad in (-1, 3):
+        o = kt.options(lane_variant=bad)
+        rc = L.kt_integrate_ptrs(net.ptr, 0, None, None, None, 1e-6, C.byref(o), None, None, None, None,
+                                 None, None, None)
+        assert rc == -1 and b"out of range" in L.kt_last_error()
+    for good in (kt.KT_LANE_AUTO, kt.KT_LANE_JCACHE, kt.KT_LANE_LEAN):
+        o = kt.options(lane_variant=good)
+        rc = L.kt_integrate_ptrs(net.ptr, 0, None, None, None, 1e-6, C.byref(o), None, None, None, None,
+                                 None, None, None)
+        assert rc == 0, L.kt_last_error()
+
+
 def test_no_oracle_in_product_path():
     """The CUDA package never imports, links or loads the oracle."""
     pkg = os.path.join(ROOT, "paper_2504_04941_gb300")
