@@ -88,9 +88,14 @@ def make_pairs(net: kt.Network, wl: I.Workload, n_pairs: int, seed: int,
     return dict(y0=y0[:, ok], T=T[ok], rho=rho[ok], dt=dt[ok], y1=r["y"][:, ok])
 
 
+def _t_pair(pairs):
+    """(T at the start, T at the end) of pairs with the energy equation, else (None, None)."""
+    return (pairs["T"], pairs["T1"]) if "T1" in pairs else (None, None)
+
+
 def normalisation(pairs):
     X = _features(pairs["y0"], pairs["T"], pairs["rho"], pairs["dt"])
-    D = _targets(pairs["y0"], pairs["y1"], pairs.get("T"), pairs.get("T1"))
+    D = _targets(pairs["y0"], pairs["y1"], *_t_pair(pairs))
     mu_in, sd_in = X.mean(0), X.std(0)
     mu_out, sd_out = D.mean(0), D.std(0)
     sd_in = torch_where_small(sd_in)
@@ -107,7 +112,7 @@ def normalised_tensors(pairs, norm):
     import torch
     mu_in, sd_in, mu_out, sd_out = (torch.from_numpy(np.asarray(v, np.float64)).cuda() for v in norm)
     X = (_features(pairs["y0"], pairs["T"], pairs["rho"], pairs["dt"]) - mu_in) / sd_in
-    D = (_targets(pairs["y0"], pairs["y1"], pairs.get("T"), pairs.get("T1")) - mu_out) / sd_out
+    D = (_targets(pairs["y0"], pairs["y1"], *_t_pair(pairs)) - mu_out) / sd_out
     return X.float().contiguous(), D.float().contiguous()
 
 
