@@ -317,7 +317,8 @@ void build_blob(kt_network *n)
     v.off_cnt = o; o = align16(o + 8 * n->ns * n->ne);
     v.off_idx = o; o = align16(o + 8 * n->nr);
     v.off_exp = o; o = align16(o + 8 * kt::kExpTable);
-    // per-species lists of (reaction, net coefficient)
+    // per-species lists of (reaction, +-1): a net coefficient nu appears as |nu| entries
+    // of its sign, so every entry is one add (no per-lane branch on the coefficient)
     std::vector<int> rp(n->ns + 1, 0), re;
     for (int s = 0; s < n->ns; ++s) {
         rp[s] = static_cast<int>(re.size());
@@ -325,7 +326,7 @@ void build_blob(kt_network *n)
             int nu = 0;
             for (int j = 0; j < n->nout[r]; ++j) nu += n->out[r][j] == s;
             for (int j = 0; j < n->nin[r]; ++j) nu -= n->in[r][j] == s;
-            if (nu != 0) re.push_back((r << 8) | (nu & 0xff));
+            for (int q = 0; q < (nu < 0 ? -nu : nu); ++q) re.push_back((r << 8) | ((nu < 0 ? -1 : 1) & 0xff));
         }
     }
     rp[n->ns] = static_cast<int>(re.size());

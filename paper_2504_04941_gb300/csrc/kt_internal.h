@@ -36,7 +36,8 @@ struct NetView {
     int off_exp;                          // double[kExpTable]: 2^(j/256) for the table-driven exp
     int off_rp, off_re, nent;             // per-species reaction lists (CSR): int32 row
                                           // pointers [ns+1]; entries (r << 8) | (nu & 0xff),
-                                          // nu = net stoichiometric coefficient (nonzero)
+                                          // nu = +-1: a net stoichiometric coefficient of
+                                          // magnitude m appears as m entries
     int shape;                            // 22: every reaction has 2 reactants and 2
                                           // products (straight-line rate code); 0: mixed
     int cvpoly, off_cvp;                  // heat capacities polynomial in T: double[ns*10],

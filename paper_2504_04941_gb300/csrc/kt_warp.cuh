@@ -341,10 +341,11 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 2) warp_kernel(const LaunchArg
     auto rows = [&](const double *yt, bool wantJ) {
         if (!wantJ) {
             // f alone: each reaction's rate w_r = k_r n_i n_j (n_k) once, lanes over
-            // reactions, then every species row adds +-w_r (a coefficient of +-2 as an
-            // FMA) in its list's order.  The same sums, bit for bit, as forming
-            // nu (k n_i n_j) entry by entry, with about a quarter of the FP64 work: a
-            // reaction appears in four rows.
+            // reactions, then every species row adds +-w_r per list entry (every entry
+            // has a coefficient of +-1), the sign applied on the bit pattern: one FP64
+            // add per entry whatever the signs of the 32 rows a warp sums at once, and
+            // about a quarter of the FP64 work of forming k n_i n_j in every row a
+            // reaction appears in.
             for (int r = lane; r < nr; r += 32) {
                 const unsigned long long ix = t.idx[r];
                 const int nin = static_cast<int>(ix & 0x7f);
@@ -359,11 +360,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32, 2) warp_kernel(const LaunchArg
                 const int e1 = t.rp[s + 1];
                 for (int e = t.rp[s]; e < e1; ++e) {
                     const int ent = t.re[e];
-                    const int nu = static_cast<signed char>(ent & 0xff);
-                    const double w = RW[ent >> 8];
-                    if (nu == 1) f += w;
-                    else if (nu == -1) f -= w;
-                    else f = fma(static_cast<double>(nu), w, f);
+                    // -1 is stored as 0xff: its bit 7 becomes the sign bit of w_r
+                    const long long sign = static_cast<long long>(ent & 0x80) << 56;
+                    f += __longlong_as_double(__double_as_longlong(RW[ent >> 8]) ^ sign);
                 }
                 W[s] = f;
             }
