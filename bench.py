@@ -5,11 +5,14 @@ cells advanced over the full dt): rates, Jacobian, LU, solve and adaptive sub-st
 for every cell.  Default workload: the combustion-like network (10 species,
 2 elements, 30 reversible reactions, temperature equation), 65,536 cells, dt = 1e-6 s.
 
-Printed JSON line (rank 0): value = the chosen form's cells/s (FP32-LU simplified
-Newton, persistent kernel), with the plain FP64 form alongside under "forms";
-"e2e" = the same metric through kt_state upload / integrate / download with pinned
-host buffers; "roofline" = algorithmic FLOP/s of the integrate kernel against the
-FP64 pipe peak; "cpu_baseline" = the FP64 oracle on a bounded sample on the host.
+Printed JSON line (rank 0): value = the chosen form's cells/s (TR-BDF2 sub-steps,
+FP32-LU simplified Newton, persistent longest-first queue replayed from a CUDA graph,
+the queue ordered by the next interval's Newton counts), with the plain FP64 forms
+(backward Euler and TR-BDF2) alongside under "forms"; "e2e" = the same metric through
+kt_state upload / integrate / download with pinned host buffers; "roofline" =
+algorithmic FLOP/s of the integrate kernel against the FP64 pipe peak measured in the
+run; "cpu_baseline" = the FP64 oracle on a bounded sample on the host.
+--workload 3 / 5 with --ncells run the ISM and the 64-species networks.
 
 --impl reference times the FP64 CPU oracle itself on the host cores.
 """
