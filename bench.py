@@ -199,12 +199,13 @@ def hbm_peak_gbs() -> tuple:
 SCHEME_NAMES = {0: "be_step_doubling", 1: "trbdf2"}
 
 
-def oracle_on(network: I.Network, cells: I.Cells, tol: I.Tolerances, scheme: int = 0):
-    """The FP64 oracle (as it stands) on these cells with all host cores; returns
-    (result dict, threads, wall seconds)."""
+def oracle_on(network: I.Network, cells: I.Cells, tol: I.Tolerances, scheme: int = 0,
+              threads: int = 0):
+    """The FP64 oracle (as it stands) on these cells with all host cores (or `threads`);
+    returns (result dict, threads, wall seconds)."""
     from oracle import oracle
     net = oracle.OracleNetwork(network)
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     t0 = time.perf_counter()
     r = net.integrate(cells, tol.dt, oracle.options(tol, scheme=scheme), threads)
     return r, threads, time.perf_counter() - t0
@@ -520,6 +521,11 @@ def main():
                          f"{wall:.1f} s wall"}
         for scheme, (_, thr, w) in ora.items():
             cpu[f"value_{SCHEME_NAMES[scheme]}"] = nsample / w
+        # one host thread on the first 128 cells of the same sample (the chosen scheme)
+        n1 = min(128, nsample)
+        _, _, w1 = oracle_on(wl.network, sample.subset(range(n1)), wl.tol, scheme=head_scheme, threads=1)
+        cpu["value_1thread"] = n1 / w1
+        cpu["sample_1thread"] = f"first {n1} cells of the sample, 1 thread, {w1:.1f} s wall"
         for name in results:
             try:
                 so = kt.options(wl.tol, **forms[name])
