@@ -522,10 +522,13 @@ def main():
         for scheme, (_, thr, w) in ora.items():
             cpu[f"value_{SCHEME_NAMES[scheme]}"] = nsample / w
         # one host thread on the first 128 cells of the same sample (the chosen scheme)
-        n1 = min(128, nsample)
-        _, _, w1 = oracle_on(wl.network, sample.subset(range(n1)), wl.tol, scheme=head_scheme, threads=1)
-        cpu["value_1thread"] = n1 / w1
-        cpu["sample_1thread"] = f"first {n1} cells of the sample, 1 thread, {w1:.1f} s wall"
+        try:
+            n1 = min(128, nsample)
+            _, _, w1 = oracle_on(wl.network, sample.subset(range(n1)), wl.tol, scheme=head_scheme, threads=1)
+            cpu["value_1thread"] = n1 / w1
+            cpu["sample_1thread"] = f"first {n1} cells of the sample, 1 thread, {w1:.1f} s wall"
+        except Exception as ex:              # a report, never a reason to lose the line
+            cpu["value_1thread"] = {"error": repr(ex)[:300]}
         for name in results:
             try:
                 so = kt.options(wl.tol, **forms[name])
