@@ -165,12 +165,15 @@ KT_API int kt_network_info(const kt_network *net, int *n_species, int *n_element
 
 KT_API void kt_network_free(kt_network *net);
 
-/* Device state for ncells cells on the current CUDA device: y [n_species][ncells],
- * T, rho, status, counters, plus the scratch of the integrate call.  The library owns
- * every buffer; free with kt_state_free.  ncells may be 0. */
+/* Device state for ncells cells on the current CUDA device: what the thermochemistry
+ * step keeps per cell (Sec. 2.2, Eq. method-ode-thermochem: the species number
+ * densities, the temperature, the density), y [n_species][ncells], T, rho, plus the
+ * status, the counters and the scratch of the integrate call.  The library owns every
+ * buffer; free with kt_state_free.  ncells may be 0. */
 KT_API int kt_state_create(const kt_network *net, int64_t ncells, kt_state **out);
 
-/* Copy cell data into the state (host or device source, SoA float64).  rho may be
+/* Copy cell data into the state (host or device source, SoA float64): the cells'
+ * state before the step, which the step pre-processes (Sec. 2.2.2).  rho may be
  * NULL (then 1).  Asynchronous on stream; host sources must stay valid until the
  * copy has run (pinned memory makes the copy truly asynchronous). */
 KT_API int kt_state_upload(kt_state *st, const double *y, const double *T, const double *rho,
@@ -185,12 +188,17 @@ KT_API int kt_state_upload(kt_state *st, const double *y, const double *T, const
  * stream, same source rules as kt_state_upload. */
 KT_API int kt_state_set_cost(kt_state *st, const int32_t *cost, int src_is_device, void *cuda_stream);
 
-/* Advance every cell of the state by dt in place (asynchronous on stream).  With
+/* Advance every cell of the state by dt in place (asynchronous on stream): one
+ * thermochemistry step of Sec. 2.2 per cell, i.e. pre-processing (Sec. 2.2.2), implicit
+ * sub-steps with the rates and Jacobian of Sec. 2.2.1 factorised by Algorithm
+ * lu-decomp, post-processing and failure handling (Sec. 2.2.3).  With
  * opts->use_graph the call (scratch reset + kernel) is captured once into a CUDA graph
  * on a private stream and replayed on `stream` while dt and *opts are unchanged. */
 KT_API int kt_integrate(kt_state *st, double dt, const kt_options *opts, void *cuda_stream);
 
-/* Copy results out (host or device destination).  Any output pointer may be NULL.
+/* Copy results out (host or device destination): the cells' state after the step and
+ * their status (Sec. 2.2.3: OK, retried, reverted, non-finite input), accepted
+ * sub-steps and Newton iterations.  Any output pointer may be NULL.
  * With a host destination the call synchronises the stream and also reports a device
  * error recorded by the integrate kernels (KT_ETIMEOUT). */
 KT_API int kt_state_download(const kt_state *st, double *y, double *T, int32_t *status,
